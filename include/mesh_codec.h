@@ -1,0 +1,217 @@
+/*
+ * mesh_codec.h - C ABI of the GB300 spatio-temporal dynamic-mesh codec.
+ *
+ * The codec follows "Fast Spatio-temporal Compression of Dynamic 3D Meshes"
+ * (Arvanitis, Lalos, Moustakas).  Notation: n vertices with a fixed
+ * triangle connectivity, F frames (the paper's k), rank k (the paper's k_l,
+ * the number of retained rows of Eq. 10), n_c anchors (the paper's n_c,
+ * index set N).
+ *
+ * Conventions for every entry point
+ *   - Every pointer argument is owned by the caller and is only read or
+ *     written during the call (and, for device pointers, by work the call
+ *     enqueues on `stream`).  Nothing is retained after the call returns
+ *     except inside the handle.
+ *   - "device" pointers are CUDA global-memory addresses of the current
+ *     device; "host" pointers are ordinary (pageable or pinned) host memory.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Device work is enqueued on it in order.
+ *   - No entry point throws, aborts or traps; every failure is reported as a
+ *     mesh_codec_status_t.  A handle is not thread-safe: use one handle per
+ *     host thread and stream.
+ *   - Sizes are in elements unless a name ends in `_bytes`.
+ */
+#ifndef MESH_CODEC_H
+#define MESH_CODEC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define MESH_CODEC_API __attribute__((visibility("default")))
+#else
+#define MESH_CODEC_API
+#endif
+
+#define MESH_CODEC_ABI_VERSION 1
+#define MESH_CODEC_MAX_RANK 64      /* k <= 64 */
+#define MESH_CODEC_MAX_BITS 31      /* quantizer bits, 0 = raw binary64 */
+
+typedef enum mesh_codec_status {
+    MC_OK = 0,
+    MC_E_INVALID_ARG = 1,        /* NULL pointer, size or parameter out of range */
+    MC_E_BAD_MESH = 2,           /* triangle index out of range or repeated vertex */
+    MC_E_ISOLATED_VERTEX = 3,    /* a vertex in no triangle: Eq. 3 divides by d_i = 0 */
+    MC_E_OOM = 4,                /* device or pinned-host allocation failed */
+    MC_E_CUDA = 5,               /* a CUDA runtime call failed */
+    MC_E_NOT_CONVERGED = 6,      /* decoder solve hit its iteration cap; result written */
+    MC_E_BITSTREAM_CORRUPT = 7,  /* header, sizes or anchor indices inconsistent */
+    MC_E_BUFFER_TOO_SMALL = 8,   /* output capacity below the stream size; *written set */
+    MC_E_NUMERICAL = 9,          /* non-positive pivot in a Cholesky factor (rank-deficient data) */
+    MC_E_BAD_ANCHORS = 10        /* caller-supplied anchors not strictly increasing in [0, n) */
+} mesh_codec_status_t;
+
+/* Precision of the encoder's dense products and of the decoder's solve. */
+typedef enum mesh_codec_precision {
+    MC_PRECISION_FP64 = 0        /* every step in binary64 */
+} mesh_codec_precision_t;
+
+/* How the decoder forms the right-hand sides of Eq. 12. */
+typedef enum mesh_codec_solve_mode {
+    MC_SOLVE_FRAMES = 0,         /* one CG column per coordinate and frame (3F columns),
+                                    the order of Eq. 11-12 */
+    MC_SOLVE_FACTORED = 1        /* 3k + n_c columns: M Y = L^T C'^T and M G = P^T, then
+                                    X_c = Y_c U_c'^T + G a^_c (same solution, reassociated) */
+} mesh_codec_solve_mode_t;
+
+typedef struct mesh_codec_params {
+    int32_t n_vertices;          /* n >= 1 */
+    int32_t n_triangles;         /* T >= 1 */
+    int32_t n_frames;            /* F >= 1 (the paper's k) */
+    int32_t rank;                /* k, 1 <= k <= min(F, MESH_CODEC_MAX_RANK) (the paper's k_l) */
+    int32_t coeff_bits;          /* bits per coefficient symbol, 0..31 (0 = raw binary64); Eq. 10 */
+    int32_t dict_bits;           /* bits per dictionary element; the paper assumes 16 */
+    int32_t anchor_bits;         /* bits per anchor coordinate; the paper assumes 16 */
+    int32_t n_anchors;           /* n_c, 0..n; 0 leaves Eq. 12 singular (rejected by decode) */
+    int32_t laplacian_kind;      /* 0 = I - D^-1 C (Eq. 3, default), 1 = D - C (Eq. 1) */
+    int32_t precision;           /* mesh_codec_precision_t */
+    int32_t oi_sweeps;           /* orthogonal-iteration sweeps (maximum when oi_tol > 0) */
+    int32_t cg_max_iters;        /* decoder CG iteration cap per column */
+    double oi_tol;               /* stop when ||Q_new - Q Q^T Q_new||_F <= oi_tol; 0 = fixed count */
+    double cg_rtol;              /* per-column stop: ||r|| <= cg_rtol * ||b|| */
+    uint64_t seed;               /* anchors and the starting basis (splitmix64) */
+    int32_t solve_mode;          /* mesh_codec_solve_mode_t */
+    int32_t reserved[7];         /* must be zero */
+} mesh_codec_params_t;
+
+typedef struct mesh_codec_stats {
+    int32_t oi_sweeps[3];        /* sweeps done per coordinate in the last encode */
+    int32_t cg_iters_max;        /* over all CG columns of the last decode */
+    int32_t cg_iters_min;
+    int32_t cg_columns;          /* number of CG columns solved */
+    int32_t cg_not_converged;    /* columns that hit cg_max_iters */
+    int32_t reserved0;
+    double oi_change[3];         /* last subspace change per coordinate (0 when not measured) */
+    double cg_iters_mean;
+    double cg_rel_residual_max;  /* max over columns of ||r|| / ||b|| (recursive residual) */
+    uint64_t launches_create;    /* kernels launched by create / last encode / last decode */
+    uint64_t launches_encode;
+    uint64_t launches_decode;
+    uint64_t workspace_bytes;    /* device memory held by the handle */
+} mesh_codec_stats_t;
+
+typedef struct mesh_codec mesh_codec_t;   /* opaque handle */
+
+/* Human-readable name of a status code (static storage, never NULL). */
+MESH_CODEC_API const char* mesh_codec_status_string(mesh_codec_status_t s);
+
+/* Fills *p with defaults: 12/16/16 bits, random-walk Laplacian, FP64,
+ * 30 sweeps, cg_rtol 1e-14, cg_max_iters 50000, seed 0, solve_mode FRAMES.
+ * Sizes (n, T, F, k, n_c) are zeroed and must be set by the caller. */
+MESH_CODEC_API void mesh_codec_default_params(mesh_codec_params_t* p);
+
+/* Creates a codec for one fixed connectivity (the paper's L is built once
+ * from it and is the same for all frames, Section III).
+ *   triangles: int32 [T][3], 0-based vertex indices, host or device
+ *              (`triangles_on_device`).
+ *   anchors:   NULL to draw n_c anchors from `seed` (the n_c vertices with the
+ *              smallest splitmix64 keys), or int32 [n_c] strictly increasing
+ *              indices in [0, n), host or device (`anchors_on_device`).
+ * Builds the CSR adjacency, degrees, the anchor set, the starting basis and
+ * allocates the device workspace for (n, F, k).  Synchronises `stream`.
+ * Errors: MC_E_INVALID_ARG, MC_E_BAD_MESH, MC_E_ISOLATED_VERTEX,
+ * MC_E_BAD_ANCHORS, MC_E_OOM, MC_E_CUDA, MC_E_NUMERICAL; *out is NULL then. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_create(const mesh_codec_params_t* params,
+                                      const int32_t* triangles, int triangles_on_device,
+                                      const int32_t* anchors, int anchors_on_device,
+                                      void* stream, mesh_codec_t** out);
+
+/* Exact size in bytes of every bitstream this handle produces. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_encoded_size(const mesh_codec_t* h, size_t* bytes);
+
+/* Encoder (Section III, Eq. 7-10).
+ *   positions: device float64 [F][n][3] (frame-major, the sequence
+ *              A = [M_1; ...; M_F] of Section II).
+ *   bitstream: device bytes, `capacity` of them, 8-byte aligned; receives
+ *              the stream: a 64-byte header ("DMC1", version 1, n, F, k,
+ *              n_c, the three bit counts, the Laplacian kind, the total
+ *              size), the anchor indices, then per coordinate the quantizer
+ *              ranges (f64 lo/hi per dictionary column, per coefficient row,
+ *              and for the anchors) and three symbol sections (dictionary in
+ *              column-major order, coefficients row-major, anchors
+ *              anchor-major), each packed as bit planes of 32-symbol groups
+ *              (word g*b + j holds bit j of symbols 32g..32g+31) and padded
+ *              to 8 bytes; raw binary64 values when a bit count is 0.
+ *   written:   host; set to the stream size, also on MC_E_BUFFER_TOO_SMALL
+ *              (nothing is enqueued then).
+ * Synchronises `stream` once at the end to read the device status word.
+ * Errors: MC_E_INVALID_ARG, MC_E_BUFFER_TOO_SMALL, MC_E_NUMERICAL, MC_E_CUDA. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_encode(mesh_codec_t* h, const double* positions,
+                                      uint8_t* bitstream, size_t capacity, size_t* written,
+                                      void* stream);
+
+/* Decoder (Eq. 11-12, parallel anchored reconstruction over all frames).
+ *   bitstream:     device bytes, `bytes` of them, produced by a handle with
+ *                  the same parameters and connectivity.
+ *   positions_out: device float64 [F][n][3].
+ * Reads the 64-byte header back to the host (one synchronisation) and the
+ * status word at the end (a second one).  MC_E_NOT_CONVERGED still writes
+ * the best iterate.
+ * Errors: MC_E_INVALID_ARG, MC_E_BITSTREAM_CORRUPT, MC_E_NOT_CONVERGED,
+ * MC_E_CUDA. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_decode(mesh_codec_t* h, const uint8_t* bitstream, size_t bytes,
+                                      double* positions_out, void* stream);
+
+/* Same as encode / decode with HOST buffers: the call copies the input to
+ * the device, runs the codec and copies the result back before returning.
+ * Host memory may be pageable; pinned memory copies faster. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_encode_host(mesh_codec_t* h, const double* positions_host,
+                                           uint8_t* bitstream_host, size_t capacity,
+                                           size_t* written, void* stream);
+MESH_CODEC_API mesh_codec_status_t mesh_codec_decode_host(mesh_codec_t* h, const uint8_t* bitstream_host,
+                                           size_t bytes, double* positions_out_host,
+                                           void* stream);
+
+/* Statistics of the last create / encode / decode (synchronises the handle's
+ * last stream). */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_get_stats(const mesh_codec_t* h, mesh_codec_stats_t* st);
+
+/* Internal buffers, for inspection and testing.  Copies `count` elements of
+ * buffer `which` into the device buffer `dst` (enqueued on `stream`).
+ * `count` must equal the buffer's size, which mesh_codec_buffer_size reports.
+ *   MC_BUF_ROW_PTR   int32 [n+1]      CSR row offsets of the adjacency (no diagonal)
+ *   MC_BUF_COL_IDX   int32 [nnz]      column indices, ascending within each row
+ *   MC_BUF_DEGREE    int32 [n]        d_i = |Psi_i|
+ *   MC_BUF_ANCHORS   int32 [n_c]      anchor indices, ascending
+ *   MC_BUF_DELTA     float64 [n][3F]  delta coordinates of the last encode, vertex-major
+ *                                     (column c*F + f = coordinate c, frame f)
+ *   MC_BUF_BASIS     float64 [3][F][k] the dictionaries U_c of the last encode
+ *   MC_BUF_RITZ      float64 [3][k]   Ritz values (descending) of the last encode
+ *   MC_BUF_COEFF     float64 [3][k][n] the projections C_c = U_c^T delta_c^T (Eq. 9)
+ *   MC_BUF_START     float64 [3][F][k] the starting bases Q0_c
+ *   MC_BUF_DELTA_REC float64 [n][3F]  decoded delta coordinates of the last decode
+ *   MC_BUF_CG_ITERS  int32 [columns]  CG iterations per column of the last decode */
+typedef enum mesh_codec_buffer {
+    MC_BUF_ROW_PTR = 0, MC_BUF_COL_IDX = 1, MC_BUF_DEGREE = 2, MC_BUF_ANCHORS = 3,
+    MC_BUF_DELTA = 4, MC_BUF_BASIS = 5, MC_BUF_RITZ = 6, MC_BUF_COEFF = 7,
+    MC_BUF_START = 8, MC_BUF_DELTA_REC = 9, MC_BUF_CG_ITERS = 10
+} mesh_codec_buffer_t;
+
+MESH_CODEC_API mesh_codec_status_t mesh_codec_buffer_size(const mesh_codec_t* h, int which,
+                                           size_t* count, size_t* elem_bytes);
+MESH_CODEC_API mesh_codec_status_t mesh_codec_copy_buffer(const mesh_codec_t* h, int which,
+                                           void* dst, size_t count, void* stream);
+
+/* Frees the handle and its workspace (synchronises the device first).
+ * NULL is accepted. */
+MESH_CODEC_API void mesh_codec_destroy(mesh_codec_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MESH_CODEC_H */

@@ -1,0 +1,284 @@
+"""Python binding of libmesh_codec (include/mesh_codec.h).
+
+Argument marshalling only: every step of the codec runs in the library's
+CUDA kernels.  PyTorch provides device memory and streams; there is no CPU
+fallback, and importing this module fails loudly when the library has not
+been built.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+# ---------------------------------------------------------------- ABI mirror
+MC_OK = 0
+STATUS_NAMES = {
+    0: "MC_OK", 1: "MC_E_INVALID_ARG", 2: "MC_E_BAD_MESH", 3: "MC_E_ISOLATED_VERTEX",
+    4: "MC_E_OOM", 5: "MC_E_CUDA", 6: "MC_E_NOT_CONVERGED", 7: "MC_E_BITSTREAM_CORRUPT",
+    8: "MC_E_BUFFER_TOO_SMALL", 9: "MC_E_NUMERICAL", 10: "MC_E_BAD_ANCHORS",
+}
+MC_PRECISION_FP64 = 0
+MC_SOLVE_FRAMES = 0
+MC_SOLVE_FACTORED = 1
+
+BUF_ROW_PTR, BUF_COL_IDX, BUF_DEGREE, BUF_ANCHORS = 0, 1, 2, 3
+BUF_DELTA, BUF_BASIS, BUF_RITZ, BUF_COEFF, BUF_START = 4, 5, 6, 7, 8
+BUF_DELTA_REC, BUF_CG_ITERS = 9, 10
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("n_vertices", ctypes.c_int32), ("n_triangles", ctypes.c_int32),
+        ("n_frames", ctypes.c_int32), ("rank", ctypes.c_int32),
+        ("coeff_bits", ctypes.c_int32), ("dict_bits", ctypes.c_int32),
+        ("anchor_bits", ctypes.c_int32), ("n_anchors", ctypes.c_int32),
+        ("laplacian_kind", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("oi_sweeps", ctypes.c_int32), ("cg_max_iters", ctypes.c_int32),
+        ("oi_tol", ctypes.c_double), ("cg_rtol", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("solve_mode", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 7),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("oi_sweeps", ctypes.c_int32 * 3), ("cg_iters_max", ctypes.c_int32),
+        ("cg_iters_min", ctypes.c_int32), ("cg_columns", ctypes.c_int32),
+        ("cg_not_converged", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("oi_change", ctypes.c_double * 3), ("cg_iters_mean", ctypes.c_double),
+        ("cg_rel_residual_max", ctypes.c_double), ("launches_create", ctypes.c_uint64),
+        ("launches_encode", ctypes.c_uint64), ("launches_decode", ctypes.c_uint64),
+        ("workspace_bytes", ctypes.c_uint64),
+    ]
+
+    def as_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
+
+
+class MeshCodecError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        self.name = STATUS_NAMES.get(status, str(status))
+        super().__init__(f"{where}: {self.name} ({status})")
+
+
+_LIB = None
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "mesh_codec_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "mesh_codec_default_params": (None, [ctypes.POINTER(Params)]),
+    "mesh_codec_create": (ctypes.c_int, [ctypes.POINTER(Params), _P, ctypes.c_int, _P,
+                                         ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    "mesh_codec_encoded_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "mesh_codec_encode": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t,
+                                         ctypes.POINTER(ctypes.c_size_t), _P]),
+    "mesh_codec_decode": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, _P]),
+    "mesh_codec_encode_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t,
+                                              ctypes.POINTER(ctypes.c_size_t), _P]),
+    "mesh_codec_decode_host": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, _P]),
+    "mesh_codec_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
+    "mesh_codec_buffer_size": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t),
+                                              ctypes.POINTER(ctypes.c_size_t)]),
+    "mesh_codec_copy_buffer": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t, _P]),
+    "mesh_codec_destroy": (None, [_P]),
+}
+
+
+def library_path():
+    return _build.LIB
+
+
+def load_library(build_if_missing=False):
+    """Load libmesh_codec.so (building it first when asked).  Raises
+    ImportError when the library is absent: there is no fallback path."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if build_if_missing and not os.path.exists(path):
+        _build.build()
+    if not os.path.exists(path):
+        raise ImportError(f"libmesh_codec.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def default_params():
+    p = Params()
+    load_library().mesh_codec_default_params(ctypes.byref(p))
+    return p
+
+
+def _check(status, where):
+    if status != MC_OK:
+        raise MeshCodecError(status, where)
+
+
+def _torch():
+    import torch  # noqa: WPS433  (device memory and streams only)
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class MeshCodec:
+    """One codec handle for a fixed connectivity (see mesh_codec_create).
+
+    tris: int32 [T, 3] (numpy or a CUDA tensor).  Keyword arguments set
+    fields of mesh_codec_params_t (n_frames, rank, n_anchors, coeff_bits, ...).
+    """
+
+    def __init__(self, tris, n_vertices, anchors=None, stream=None, **kw):
+        torch = _torch()
+        lib = load_library()
+        p = default_params()
+        p.n_vertices = int(n_vertices)
+        p.n_triangles = int(tris.shape[0])
+        for key, val in kw.items():
+            if not hasattr(p, key):
+                raise TypeError(f"unknown parameter {key}")
+            setattr(p, key, val)
+        self.params = p
+        if isinstance(tris, np.ndarray):
+            tri_t = torch.from_numpy(np.ascontiguousarray(tris, dtype=np.int32)).cuda()
+        else:
+            tri_t = tris.to(device="cuda", dtype=torch.int32).contiguous()
+        anc_ptr = None
+        self._anc_t = None
+        if anchors is not None:
+            self._anc_t = torch.as_tensor(np.asarray(anchors, dtype=np.int32)).cuda()
+            anc_ptr = ctypes.c_void_p(self._anc_t.data_ptr())
+        h = ctypes.c_void_p()
+        st = lib.mesh_codec_create(ctypes.byref(p), ctypes.c_void_p(tri_t.data_ptr()), 1, anc_ptr,
+                                   1, _stream_ptr(stream), ctypes.byref(h))
+        _check(st, "mesh_codec_create")
+        self._h = h
+        self._lib = lib
+        size = ctypes.c_size_t()
+        _check(lib.mesh_codec_encoded_size(h, ctypes.byref(size)), "mesh_codec_encoded_size")
+        self.stream_bytes = size.value
+        self.n, self.F, self.k = p.n_vertices, p.n_frames, p.rank
+
+    # ------------------------------------------------------------ device API
+    def encode(self, positions, out=None, stream=None):
+        """positions: CUDA float64 [F, n, 3] -> CUDA uint8 bitstream."""
+        torch = _torch()
+        assert positions.is_cuda and positions.dtype == torch.float64
+        assert tuple(positions.shape) == (self.F, self.n, 3) and positions.is_contiguous()
+        if out is None:
+            out = torch.empty(self.stream_bytes, dtype=torch.uint8, device=positions.device)
+        written = ctypes.c_size_t()
+        st = self._lib.mesh_codec_encode(self._h, ctypes.c_void_p(positions.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()), out.numel(),
+                                         ctypes.byref(written), _stream_ptr(stream))
+        _check(st, "mesh_codec_encode")
+        return out[: written.value]
+
+    def decode(self, bitstream, out=None, stream=None, allow_not_converged=False):
+        torch = _torch()
+        assert bitstream.is_cuda and bitstream.dtype == torch.uint8
+        if out is None:
+            out = torch.empty((self.F, self.n, 3), dtype=torch.float64, device=bitstream.device)
+        st = self._lib.mesh_codec_decode(self._h, ctypes.c_void_p(bitstream.data_ptr()),
+                                         bitstream.numel(), ctypes.c_void_p(out.data_ptr()),
+                                         _stream_ptr(stream))
+        if not (allow_not_converged and st == 6):
+            _check(st, "mesh_codec_decode")
+        return out
+
+    # ------------------------------------------------------------ host API
+    def encode_host(self, positions, out=None, stream=None):
+        """positions: numpy / pinned CPU tensor float64 [F, n, 3] -> host bytes."""
+        ptr, keep = _host_ptr(positions, np.float64, (self.F, self.n, 3))
+        if out is None:
+            out = np.empty(self.stream_bytes, dtype=np.uint8)
+        optr, okeep = _host_ptr(out, np.uint8, None)
+        written = ctypes.c_size_t()
+        st = self._lib.mesh_codec_encode_host(self._h, ptr, optr, self.stream_bytes,
+                                              ctypes.byref(written), _stream_ptr(stream))
+        _check(st, "mesh_codec_encode_host")
+        del keep, okeep
+        return out
+
+    def decode_host(self, bitstream, out=None, stream=None):
+        ptr, keep = _host_ptr(bitstream, np.uint8, None)
+        if out is None:
+            out = np.empty((self.F, self.n, 3), dtype=np.float64)
+        optr, okeep = _host_ptr(out, np.float64, (self.F, self.n, 3))
+        nbytes = bitstream.numel() if hasattr(bitstream, "numel") else len(bitstream)
+        st = self._lib.mesh_codec_decode_host(self._h, ptr, nbytes, optr, _stream_ptr(stream))
+        _check(st, "mesh_codec_decode_host")
+        del keep, okeep
+        return out
+
+    # ------------------------------------------------------------ inspection
+    def stats(self):
+        s = Stats()
+        _check(self._lib.mesh_codec_get_stats(self._h, ctypes.byref(s)), "mesh_codec_get_stats")
+        return s.as_dict()
+
+    def buffer(self, which, stream=None):
+        torch = _torch()
+        cnt, eb = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(self._lib.mesh_codec_buffer_size(self._h, which, ctypes.byref(cnt), ctypes.byref(eb)),
+               "mesh_codec_buffer_size")
+        dt = {4: torch.int32, 8: torch.float64}[eb.value]
+        out = torch.empty(max(cnt.value, 1), dtype=dt, device="cuda")
+        _check(self._lib.mesh_codec_copy_buffer(self._h, which, ctypes.c_void_p(out.data_ptr()),
+                                                cnt.value, _stream_ptr(stream)),
+               "mesh_codec_copy_buffer")
+        return out[: cnt.value]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mesh_codec_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _host_ptr(obj, dtype, shape):
+    if isinstance(obj, np.ndarray):
+        a = obj
+        if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host buffer must be C-contiguous with the right dtype")
+        if shape is not None and a.shape != shape:
+            raise ValueError(f"host buffer shape {a.shape} != {shape}")
+        return ctypes.c_void_p(a.ctypes.data), a
+    torch = _torch()
+    if isinstance(obj, torch.Tensor) and obj.device.type == "cpu":
+        if not obj.is_contiguous():
+            raise ValueError("host tensor must be contiguous")
+        return ctypes.c_void_p(obj.data_ptr()), obj
+    if isinstance(obj, (bytes, bytearray)):
+        a = np.frombuffer(obj, dtype=np.uint8)
+        return ctypes.c_void_p(a.ctypes.data), a
+    raise TypeError("unsupported host buffer")

@@ -1,0 +1,653 @@
+// C ABI of the codec (include/mesh_codec.h): handle, workspace and the order
+// in which the encoder and decoder enqueue their kernels.
+//
+// Encoder, per call (Section III, Fig. 1):
+//   ingest [F][n][3] -> X [n][3F]; delta = L X (Eq. 3/4, Eq. 8);
+//   orthogonal iterations Q <- qr(A_c (A_c^T Q)) (Algorithm 1, Eq. 7) for the
+//   three coordinates at once; Rayleigh-Ritz (eigen-order, sign); projection
+//   C_c = U_c^T delta_c^T (Eq. 9, first k rows = Eq. 10's truncation);
+//   quantize + pack dictionary, coefficients and anchor positions.
+// Decoder (Eq. 11-12): unpack; delta~ = (U' C')^T; B = L^T delta~ + P^T a^;
+//   Jacobi-CG on (L^T L + P^T P) X = B over all 3F columns; X -> [F][n][3].
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mc_internal.cuh"
+
+using namespace mc;
+
+struct mesh_codec {
+  mesh_codec_params_t p;
+  int n, T, F, k, W, n_c, kind;
+  EncodeLayout lay;
+  CgGeom geom;
+  // device workspace (one allocation)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  int32_t *row_ptr, *col_idx, *deg, *anchors, *dec_anchors;
+  uint8_t* is_anchor;
+  double *inv_d, *inv_diag;
+  double *Q0, *Q, *Zb, *U, *V, *H, *theta, *Wk, *partials, *chg_work, *chg;
+  double *G, *Rf;
+  double *Cf, *qparams;
+  double *X, *D, *B, *R, *P, *Tv, *Qv;
+  double *Udeq, *Cdeq, *Ahat;
+  CgState cg;
+  uint32_t* d_status;
+  int nnz;
+  size_t partial_elems;
+  // host side
+  uint32_t* h_status = nullptr;     // pinned
+  int32_t* h_active = nullptr;      // pinned
+  uint8_t* h_header = nullptr;      // pinned, 64 bytes
+  double* h_chg = nullptr;          // pinned [3]
+  // staging for the host-buffer entry points (lazy)
+  double* stage_pos = nullptr;
+  uint8_t* stage_bits = nullptr;
+  cudaStream_t last_stream = nullptr;
+  uint64_t launches_create = 0, launches_encode = 0, launches_decode = 0;
+  int oi_done[3] = {0, 0, 0};
+  double oi_last_change[3] = {0, 0, 0};
+  int cg_columns = 0;
+};
+
+namespace {
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base((char*)b) {}
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? (T*)(base + off) : nullptr;
+    off += sizeof(T) * std::max<size_t>(count, 1);
+    return p;
+  }
+};
+
+// lay out (or measure, when base == nullptr) the workspace
+size_t carve(mesh_codec* h, void* base) {
+  Carver c(base);
+  const size_t n = h->n, F = h->F, k = h->k, W = h->W, nc = std::max(h->n_c, 1);
+  const size_t nnz_max = 6ull * h->T;
+  h->row_ptr = c.take<int32_t>(n + 1);
+  h->col_idx = c.take<int32_t>(nnz_max);
+  h->deg = c.take<int32_t>(n);
+  h->anchors = c.take<int32_t>(nc);
+  h->dec_anchors = c.take<int32_t>(nc);
+  h->is_anchor = c.take<uint8_t>(n);
+  h->inv_d = c.take<double>(n);
+  h->inv_diag = c.take<double>(n);
+  h->Q0 = c.take<double>(3 * F * k);
+  h->Q = c.take<double>(3 * F * k);
+  h->Zb = c.take<double>(3 * F * k);
+  h->U = c.take<double>(3 * F * k);
+  h->V = c.take<double>(3 * k * k);
+  h->H = c.take<double>(3 * k * k);
+  h->G = c.take<double>(3 * k * k);
+  h->Rf = c.take<double>(3 * k * k);
+  h->theta = c.take<double>(3 * k);
+  h->Wk = c.take<double>(3 * n * k);
+  h->partials = c.take<double>(h->partial_elems);
+  h->chg_work = c.take<double>(3 * k * k + 3 * F * k);
+  h->chg = c.take<double>(3);
+  h->Cf = c.take<double>(3 * k * n);
+  h->qparams = c.take<double>(3 * (4 * k + 2));
+  h->X = c.take<double>(n * W);
+  h->D = c.take<double>(n * W);
+  h->B = c.take<double>(n * W);
+  h->R = c.take<double>(n * W);
+  h->P = c.take<double>(n * W);
+  h->Tv = c.take<double>(n * W);
+  h->Qv = c.take<double>(n * W);
+  h->Udeq = c.take<double>(3 * F * k);
+  h->Cdeq = c.take<double>(3 * k * n);
+  h->Ahat = c.take<double>(3 * nc * F);
+  h->cg.rz = c.take<double>(W);
+  h->cg.rr = c.take<double>(W);
+  h->cg.bb = c.take<double>(W);
+  h->cg.pap = c.take<double>(W);
+  h->cg.alpha = c.take<double>(W);
+  h->cg.beta = c.take<double>(W);
+  h->cg.done = c.take<int32_t>(W);
+  h->cg.iters = c.take<int32_t>(W);
+  h->cg.partials = c.take<double>(cg_partials_elems(h->n, h->W));
+  h->cg.active = c.take<int32_t>(1);
+  h->cg.all_done = c.take<int32_t>(1);
+  h->d_status = c.take<uint32_t>(4);
+  return c.off + 256;
+}
+
+int gemm_splits(long long K, long long tiles) {
+  // enough split-K CTAs to cover the SMs several times, at least 64 k per split
+  long long want = std::max<long long>(1, (152 * 8) / std::max<long long>(1, tiles));
+  long long maxs = std::max<long long>(1, K / 64);
+  return (int)std::min(want, maxs);
+}
+
+mesh_codec_status_t cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return MC_OK;
+  if (e == cudaErrorMemoryAllocation) return MC_E_OOM;
+  return MC_E_CUDA;
+}
+
+#define MC_TRY(expr)                                  \
+  do {                                                \
+    cudaError_t _e = (expr);                          \
+    if (_e != cudaSuccess) return cuda_status(_e);    \
+  } while (0)
+
+mesh_codec_status_t status_from_bits(uint32_t bits) {
+  if (bits & ST_BAD_INDEX) return MC_E_BAD_MESH;
+  if (bits & ST_DEGENERATE) return MC_E_BAD_MESH;
+  if (bits & ST_ISOLATED) return MC_E_ISOLATED_VERTEX;
+  if (bits & ST_BAD_ANCHORS) return MC_E_BAD_ANCHORS;
+  if (bits & ST_BITSTREAM) return MC_E_BITSTREAM_CORRUPT;
+  if (bits & ST_CHOL_BREAKDOWN) return MC_E_NUMERICAL;
+  if (bits & ST_NOT_CONVERGED) return MC_E_NOT_CONVERGED;
+  return MC_OK;
+}
+
+mesh_codec_status_t read_status(mesh_codec* h, cudaStream_t s) {
+  MC_TRY(cudaMemcpyAsync(h->h_status, h->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  MC_TRY(cudaStreamSynchronize(s));
+  MC_TRY(cudaGetLastError());
+  return status_from_bits(*h->h_status);
+}
+
+bool valid_params(const mesh_codec_params_t* p) {
+  if (!p) return false;
+  if (p->n_vertices < 1 || p->n_triangles < 1 || p->n_frames < 1) return false;
+  if (p->rank < 1 || p->rank > p->n_frames || p->rank > MESH_CODEC_MAX_RANK) return false;
+  if (p->coeff_bits < 0 || p->coeff_bits > MESH_CODEC_MAX_BITS) return false;
+  if (p->dict_bits < 0 || p->dict_bits > MESH_CODEC_MAX_BITS) return false;
+  if (p->anchor_bits < 0 || p->anchor_bits > MESH_CODEC_MAX_BITS) return false;
+  if (p->n_anchors < 0 || p->n_anchors > p->n_vertices) return false;
+  if (p->laplacian_kind != 0 && p->laplacian_kind != 1) return false;
+  if (p->precision != MC_PRECISION_FP64) return false;
+  if (p->oi_sweeps < 0 || p->cg_max_iters < 1) return false;
+  if (!(p->oi_tol >= 0.0) || !(p->cg_rtol >= 0.0)) return false;
+  if (p->solve_mode != MC_SOLVE_FRAMES) return false;
+  // 3F columns x n rows must be indexable, and the per-coordinate product fit
+  if ((long long)p->n_frames * 3 > (1LL << 30)) return false;
+  if ((long long)p->n_vertices * 3 * p->n_frames > (1LL << 40)) return false;
+  for (int i = 0; i < 7; ++i)
+    if (p->reserved[i] != 0) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mesh_codec_status_string(mesh_codec_status_t s) {
+  switch (s) {
+    case MC_OK: return "ok";
+    case MC_E_INVALID_ARG: return "invalid argument";
+    case MC_E_BAD_MESH: return "bad mesh (index out of range or repeated vertex)";
+    case MC_E_ISOLATED_VERTEX: return "isolated vertex";
+    case MC_E_OOM: return "out of memory";
+    case MC_E_CUDA: return "CUDA error";
+    case MC_E_NOT_CONVERGED: return "decoder solve did not converge";
+    case MC_E_BITSTREAM_CORRUPT: return "corrupt bitstream";
+    case MC_E_BUFFER_TOO_SMALL: return "output buffer too small";
+    case MC_E_NUMERICAL: return "numerical breakdown (rank-deficient trajectories)";
+    case MC_E_BAD_ANCHORS: return "bad anchor indices";
+  }
+  return "unknown status";
+}
+
+void mesh_codec_default_params(mesh_codec_params_t* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->coeff_bits = 12;
+  p->dict_bits = 16;
+  p->anchor_bits = 16;
+  p->laplacian_kind = 0;
+  p->precision = MC_PRECISION_FP64;
+  p->oi_sweeps = 30;
+  p->cg_max_iters = 50000;
+  p->oi_tol = 0.0;
+  p->cg_rtol = 1e-14;
+  p->seed = 0;
+  p->solve_mode = MC_SOLVE_FRAMES;
+}
+
+void mesh_codec_destroy(mesh_codec_t* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  if (h->ws) cudaFree(h->ws);
+  if (h->stage_pos) cudaFree(h->stage_pos);
+  if (h->stage_bits) cudaFree(h->stage_bits);
+  if (h->h_status) cudaFreeHost(h->h_status);
+  if (h->h_active) cudaFreeHost(h->h_active);
+  if (h->h_header) cudaFreeHost(h->h_header);
+  if (h->h_chg) cudaFreeHost(h->h_chg);
+  delete h;
+}
+
+static mesh_codec_status_t create_impl(mesh_codec* h, const int32_t* tris_in, int tris_dev,
+                                       const int32_t* anchors_in, int anchors_dev,
+                                       cudaStream_t s) {
+  Launches L{&h->launches_create};
+  const int n = h->n, T = h->T;
+  h->lay = make_layout(n, h->F, h->k, h->n_c, h->p.coeff_bits, h->p.dict_bits,
+                       h->p.anchor_bits, h->kind);
+  h->geom = cg_geometry(n, h->W);
+  // split-K partial buffer: the largest of the encoder's reductions
+  {
+    size_t F = h->F, k = h->k;
+    int sz = gemm_splits(n, ((F + 63) / 64) * ((k + 31) / 32));
+    int sh = gemm_splits(n, ((k + 63) / 64) * ((k + 31) / 32));
+    int sg = gemm_splits(F, ((k + 63) / 64) * ((k + 31) / 32));
+    size_t a = (size_t)sz * 3 * F * k, b = (size_t)sh * 3 * k * k, c = (size_t)sg * 3 * k * k;
+    h->partial_elems = std::max(a, std::max(b, c));
+  }
+  h->ws_bytes = carve(h, nullptr);
+  MC_TRY(cudaMalloc(&h->ws, h->ws_bytes));
+  carve(h, h->ws);
+  MC_TRY(cudaMallocHost(&h->h_status, sizeof(uint32_t) * 4));
+  MC_TRY(cudaMallocHost(&h->h_active, sizeof(int32_t) * 4));
+  MC_TRY(cudaMallocHost(&h->h_header, 64));
+  MC_TRY(cudaMallocHost(&h->h_chg, sizeof(double) * 4));
+  MC_TRY(cudaMemsetAsync(h->d_status, 0, sizeof(uint32_t) * 4, s));
+
+  // temporaries for the CSR build
+  void* tmp = nullptr;
+  size_t tmp_bytes = 0;
+  {
+    Carver c(nullptr);
+    c.take<int32_t>(n);
+    c.take<int32_t>(n + 1);
+    c.take<int32_t>(n);
+    c.take<int32_t>(6ull * T);
+    c.take<int32_t>(scan_tmp_elems(n));
+    c.take<int32_t>(3ull * T);
+    c.take<int32_t>(std::max(h->n_c, 1));
+    tmp_bytes = c.off + 256;
+  }
+  MC_TRY(cudaMalloc(&tmp, tmp_bytes));
+  Carver c(tmp);
+  CsrBuildTmp t{};
+  t.raw_deg = c.take<int32_t>(n);
+  t.raw_off = c.take<int32_t>(n + 1);
+  t.cursor = c.take<int32_t>(n);
+  t.raw_col = c.take<int32_t>(6ull * T);
+  t.scan_tmp = c.take<int32_t>(scan_tmp_elems(n));
+  int32_t* tris_dev_buf = c.take<int32_t>(3ull * T);
+  int32_t* anchors_tmp = c.take<int32_t>(std::max(h->n_c, 1));
+  const int32_t* tris = tris_in;
+  if (!tris_dev) {
+    cudaError_t e = cudaMemcpyAsync(tris_dev_buf, tris_in, sizeof(int32_t) * 3ull * T,
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) { cudaFree(tmp); return cuda_status(e); }
+    tris = tris_dev_buf;
+  }
+  build_csr(tris, T, n, t, h->row_ptr, nullptr, h->deg, h->d_status, s, L);
+  compact_csr(t, h->row_ptr, h->col_idx, n, s, L);
+  // anchors
+  if (h->n_c > 0) {
+    if (anchors_in) {
+      const int32_t* a = anchors_in;
+      if (!anchors_dev) {
+        cudaError_t e = cudaMemcpyAsync(anchors_tmp, anchors_in, sizeof(int32_t) * h->n_c,
+                                        cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) { cudaFree(tmp); return cuda_status(e); }
+        a = anchors_tmp;
+      }
+      cudaMemcpyAsync(h->anchors, a, sizeof(int32_t) * h->n_c, cudaMemcpyDeviceToDevice, s);
+      check_anchors(h->anchors, h->n_c, n, h->d_status, s, L);
+    } else {
+      select_anchors(n, h->n_c, h->p.seed, h->anchors, s, L);
+    }
+  }
+  cudaMemsetAsync(h->is_anchor, 0, n, s);
+  mark_anchors(h->anchors, h->n_c, h->is_anchor, s, L);
+  vertex_scalars_marked(h->row_ptr, h->col_idx, h->deg, h->is_anchor, n, h->kind, h->inv_d,
+                        h->inv_diag, s, L);
+  // starting basis Q0: splitmix64 uniforms made orthonormal by CholeskyQR3
+  gen_start_basis(h->Q0, h->F, h->k, h->p.seed, s, L);
+  int sg = gemm_splits(h->F, ((h->k + 63) / 64) * ((h->k + 31) / 32));
+  cholqr3(h->Q0, h->F, h->k, h->G, h->Rf, h->partials, sg, h->d_status, s, L);
+  mesh_codec_status_t st = read_status(h, s);
+  int32_t nnz = 0;
+  if (st == MC_OK) {
+    cudaMemcpy(&nnz, h->row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    h->nnz = nnz;
+  }
+  cudaFree(tmp);
+  if (st == MC_OK) MC_TRY(cudaGetLastError());
+  return st;
+}
+
+mesh_codec_status_t mesh_codec_create(const mesh_codec_params_t* params, const int32_t* triangles,
+                                      int triangles_on_device, const int32_t* anchors,
+                                      int anchors_on_device, void* stream, mesh_codec_t** out) {
+  if (!out) return MC_E_INVALID_ARG;
+  *out = nullptr;
+  if (!valid_params(params) || !triangles) return MC_E_INVALID_ARG;
+  mesh_codec* h = new (std::nothrow) mesh_codec();
+  if (!h) return MC_E_OOM;
+  h->p = *params;
+  h->n = params->n_vertices;
+  h->T = params->n_triangles;
+  h->F = params->n_frames;
+  h->k = params->rank;
+  h->W = 3 * h->F;
+  h->n_c = params->n_anchors;
+  h->kind = params->laplacian_kind;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  mesh_codec_status_t st = create_impl(h, triangles, triangles_on_device, anchors,
+                                       anchors_on_device, s);
+  if (st != MC_OK) {
+    mesh_codec_destroy(h);
+    return st;
+  }
+  *out = h;
+  return MC_OK;
+}
+
+mesh_codec_status_t mesh_codec_encoded_size(const mesh_codec_t* h, size_t* bytes) {
+  if (!h || !bytes) return MC_E_INVALID_ARG;
+  *bytes = (size_t)h->lay.total;
+  return MC_OK;
+}
+
+static void enqueue_encode(mesh_codec* h, const double* positions, uint8_t* out, cudaStream_t s,
+                           Launches& L, bool host_check_tol) {
+  const int n = h->n, F = h->F, k = h->k, W = h->W;
+  cudaMemsetAsync(h->d_status, 0, sizeof(uint32_t), s);
+  frames_to_vertex_major(positions, h->X, F, n, s, L);
+  laplacian_rows(h->row_ptr, h->col_idx, h->deg, h->X, h->D, n, W, h->kind, s, L);
+
+  // orthogonal iterations, three coordinates batched
+  const Strided Xc{h->X, W, 1, F};        // A_c^T (n x F): element (i, f)
+  const Strided XcT{h->X, 1, W, F};       // A_c (F x n): element (f, i)
+  const int sz = gemm_splits(n, ((F + 63) / 64) * ((k + 31) / 32));
+  const int sh = gemm_splits(n, ((k + 63) / 64) * ((k + 31) / 32));
+  const int sg = gemm_splits(F, ((k + 63) / 64) * ((k + 31) / 32));
+  cudaMemcpyAsync(h->Q, h->Q0, sizeof(double) * 3 * F * k, cudaMemcpyDeviceToDevice, s);
+  for (int c = 0; c < 3; ++c) { h->oi_done[c] = 0; h->oi_last_change[c] = 0.0; }
+  for (int t = 0; t < h->p.oi_sweeps; ++t) {
+    dgemm(n, k, F, 3, Xc, Strided{h->Q, k, 1, (long long)F * k},
+          StridedOut{h->Wk, k, 1, (long long)n * k}, 1, nullptr, s, L);
+    dgemm(F, k, n, 3, XcT, Strided{h->Wk, k, 1, (long long)n * k},
+          StridedOut{h->Zb, k, 1, (long long)F * k}, sz, h->partials, s, L);
+    cholqr3(h->Zb, F, k, h->G, h->Rf, h->partials, sg, h->d_status, s, L);
+    for (int c = 0; c < 3; ++c) h->oi_done[c] = t + 1;
+    bool stop = false;
+    if (host_check_tol && h->p.oi_tol > 0.0) {
+      oi_change(h->Q, h->Zb, F, k, h->chg_work, h->chg, s, L);
+      cudaMemcpyAsync(h->h_chg, h->chg, sizeof(double) * 3, cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
+      stop = true;
+      for (int c = 0; c < 3; ++c) {
+        h->oi_last_change[c] = h->h_chg[c];
+        stop = stop && (h->h_chg[c] <= h->p.oi_tol);
+      }
+    }
+    std::swap(h->Q, h->Zb);
+    if (stop) break;
+  }
+  // Rayleigh-Ritz: H = (A_c^T Q)^T (A_c^T Q), eigenvectors V, U = Q V, signs
+  dgemm(n, k, F, 3, Xc, Strided{h->Q, k, 1, (long long)F * k},
+        StridedOut{h->Wk, k, 1, (long long)n * k}, 1, nullptr, s, L);
+  dgemm(k, k, n, 3, Strided{h->Wk, 1, k, (long long)n * k}, Strided{h->Wk, k, 1, (long long)n * k},
+        StridedOut{h->H, k, 1, (long long)k * k}, sh, h->partials, s, L);
+  jacobi_eig(h->H, h->V, h->theta, k, s, L);
+  dgemm(F, k, k, 3, Strided{h->Q, k, 1, (long long)F * k}, Strided{h->V, k, 1, (long long)k * k},
+        StridedOut{h->U, k, 1, (long long)F * k}, 1, nullptr, s, L);
+  sign_rule(h->U, F, k, s, L);
+  // projection C_c = U_c^T delta_c^T (k x n)
+  dgemm(k, n, F, 3, Strided{h->U, 1, k, (long long)F * k}, Strided{h->D, 1, W, F},
+        StridedOut{h->Cf, n, 1, (long long)k * n}, 1, nullptr, s, L);
+  // quantizer ranges: dictionary columns, coefficient rows, anchors
+  const long long P = 4LL * k + 2;
+  minmax_rows_out(h->U, k, F, 1, k, 3, (long long)F * k, h->qparams, h->qparams + k, P, s, L);
+  minmax_rows_out(h->Cf, k, n, n, 1, 3, (long long)k * n, h->qparams + 2 * k, h->qparams + 3 * k,
+                  P, s, L);
+  anchor_minmax_out(h->X, h->anchors, h->n_c, F, h->qparams + 4 * k, h->qparams + 4 * k + 1, P,
+                    s, L);
+  write_header(out, h->lay, h->anchors, h->qparams, s, L);
+  quant_pack_sections(out, h->lay, h->U, h->Cf, h->X, h->anchors, h->qparams, s, L);
+}
+
+mesh_codec_status_t mesh_codec_encode(mesh_codec_t* h, const double* positions, uint8_t* bitstream,
+                                      size_t capacity, size_t* written, void* stream) {
+  if (!h || !positions || !bitstream || !written) return MC_E_INVALID_ARG;
+  if (((uintptr_t)bitstream & 7) || ((uintptr_t)positions & 7)) return MC_E_INVALID_ARG;
+  *written = (size_t)h->lay.total;
+  if (capacity < (size_t)h->lay.total) return MC_E_BUFFER_TOO_SMALL;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  h->launches_encode = 0;
+  Launches L{&h->launches_encode};
+  enqueue_encode(h, positions, bitstream, s, L, true);
+  MC_TRY(cudaGetLastError());
+  return read_status(h, s);
+}
+
+static mesh_codec_status_t check_header(mesh_codec* h, const uint8_t* hdr, size_t bytes) {
+  uint32_t w[8];
+  std::memcpy(w, hdr, 32);
+  unsigned long long total;
+  std::memcpy(&total, hdr + 32, 8);
+  const EncodeLayout& L = h->lay;
+  if (w[0] != 0x31434D44u || w[1] != 1u || w[7] != 64u) return MC_E_BITSTREAM_CORRUPT;
+  if ((int)w[2] != L.n || (int)w[3] != L.F || (int)w[4] != L.k || (int)w[5] != L.n_c)
+    return MC_E_BITSTREAM_CORRUPT;
+  if (hdr[24] != L.cb || hdr[25] != L.db || hdr[26] != L.ab || hdr[27] != L.kind)
+    return MC_E_BITSTREAM_CORRUPT;
+  if (total != (unsigned long long)L.total || bytes != (size_t)L.total)
+    return MC_E_BITSTREAM_CORRUPT;
+  return MC_OK;
+}
+
+static mesh_codec_status_t enqueue_decode(mesh_codec* h, const uint8_t* in, double* out,
+                                          cudaStream_t s, Launches& L) {
+  const int n = h->n, F = h->F, k = h->k, W = h->W;
+  cudaMemsetAsync(h->d_status, 0, sizeof(uint32_t), s);
+  unpack_sections(in, h->lay, h->Udeq, h->Cdeq, h->Ahat, h->dec_anchors, nullptr, h->d_status, s,
+                  L);
+  // the decoder's anchor set comes from the stream
+  cudaMemsetAsync(h->is_anchor, 0, n, s);
+  mark_anchors(h->dec_anchors, h->n_c, h->is_anchor, s, L);
+  vertex_scalars_marked(h->row_ptr, h->col_idx, h->deg, h->is_anchor, n, h->kind, h->inv_d,
+                        h->inv_diag, s, L);
+  // delta~_c = (U_c' C_c')^T : (n x k)(k x F) into D[:, cF : cF + F]
+  dgemm(n, F, k, 3, Strided{h->Cdeq, 1, n, (long long)k * n}, Strided{h->Udeq, 1, k, (long long)F * k},
+        StridedOut{h->D, W, 1, F}, 1, nullptr, s, L);
+  // B = L^T delta~ + P^T a^
+  laplacian_t_rows(h->row_ptr, h->col_idx, h->deg, h->inv_d, h->D, h->B, n, W, h->kind, s, L);
+  for (int c = 0; c < 3; ++c)
+    scatter_anchor_rhs(h->B, h->Ahat + (long long)c * std::max(h->n_c, 1) * F, h->dec_anchors,
+                       h->n_c, F, W, c * F, s, L);
+  // CG
+  cg_init(h->geom, h->B, h->X, h->R, h->P, h->inv_diag, h->cg, s, L);
+  h->cg_columns = W;
+  const int batch = 32;
+  int it = 0;
+  while (it < h->p.cg_max_iters) {
+    int m = std::min(batch, h->p.cg_max_iters - it);
+    for (int j = 0; j < m; ++j)
+      cg_iteration(h->geom, h->row_ptr, h->col_idx, h->deg, h->inv_d, h->is_anchor, h->inv_diag,
+                   h->kind, h->X, h->R, h->P, h->Tv, h->Qv, h->p.cg_rtol, h->p.cg_max_iters, h->cg,
+                   s, L);
+    it += m;
+    MC_TRY(cudaMemcpyAsync(h->h_active, h->cg.active, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    MC_TRY(cudaStreamSynchronize(s));
+    if (*h->h_active == 0) break;
+  }
+  vertex_major_to_frames(h->X, out, F, n, s, L);
+  return MC_OK;
+}
+
+__global__ void k_flag_not_converged(const int32_t* done, int W, uint32_t* status) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < W; c += gridDim.x * blockDim.x)
+    if (done[c] != 1) atomicOr(status, ST_NOT_CONVERGED);
+}
+
+mesh_codec_status_t mesh_codec_decode(mesh_codec_t* h, const uint8_t* bitstream, size_t bytes,
+                                      double* positions_out, void* stream) {
+  if (!h || !bitstream || !positions_out) return MC_E_INVALID_ARG;
+  if (((uintptr_t)bitstream & 7) || ((uintptr_t)positions_out & 7)) return MC_E_INVALID_ARG;
+  if (bytes < 64) return MC_E_BITSTREAM_CORRUPT;
+  if (h->n_c == 0) return MC_E_INVALID_ARG;   // Eq. 12 needs anchors (L is singular)
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  MC_TRY(cudaMemcpyAsync(h->h_header, bitstream, 64, cudaMemcpyDeviceToHost, s));
+  MC_TRY(cudaStreamSynchronize(s));
+  mesh_codec_status_t st = check_header(h, h->h_header, bytes);
+  if (st != MC_OK) return st;
+  h->launches_decode = 0;
+  Launches L{&h->launches_decode};
+  st = enqueue_decode(h, bitstream, positions_out, s, L);
+  if (st != MC_OK) return st;
+  k_flag_not_converged<<<(h->W + 255) / 256, 256, 0, s>>>(h->cg.done, h->W, h->d_status);
+  L.add(1);
+  MC_TRY(cudaGetLastError());
+  return read_status(h, s);
+}
+
+static mesh_codec_status_t ensure_staging(mesh_codec* h) {
+  if (!h->stage_pos) MC_TRY(cudaMalloc(&h->stage_pos, sizeof(double) * 3ull * h->n * h->F));
+  if (!h->stage_bits) MC_TRY(cudaMalloc(&h->stage_bits, (size_t)h->lay.total));
+  return MC_OK;
+}
+
+mesh_codec_status_t mesh_codec_encode_host(mesh_codec_t* h, const double* positions_host,
+                                           uint8_t* bitstream_host, size_t capacity,
+                                           size_t* written, void* stream) {
+  if (!h || !positions_host || !bitstream_host || !written) return MC_E_INVALID_ARG;
+  *written = (size_t)h->lay.total;
+  if (capacity < (size_t)h->lay.total) return MC_E_BUFFER_TOO_SMALL;
+  mesh_codec_status_t st = ensure_staging(h);
+  if (st != MC_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  MC_TRY(cudaMemcpyAsync(h->stage_pos, positions_host, sizeof(double) * 3ull * h->n * h->F,
+                         cudaMemcpyHostToDevice, s));
+  h->launches_encode = 0;
+  Launches L{&h->launches_encode};
+  enqueue_encode(h, h->stage_pos, h->stage_bits, s, L, true);
+  MC_TRY(cudaMemcpyAsync(bitstream_host, h->stage_bits, (size_t)h->lay.total,
+                         cudaMemcpyDeviceToHost, s));
+  MC_TRY(cudaGetLastError());
+  return read_status(h, s);
+}
+
+mesh_codec_status_t mesh_codec_decode_host(mesh_codec_t* h, const uint8_t* bitstream_host,
+                                           size_t bytes, double* positions_out_host, void* stream) {
+  if (!h || !bitstream_host || !positions_out_host) return MC_E_INVALID_ARG;
+  if (bytes < 64) return MC_E_BITSTREAM_CORRUPT;
+  if (h->n_c == 0) return MC_E_INVALID_ARG;
+  mesh_codec_status_t st = check_header(h, bitstream_host, bytes);
+  if (st != MC_OK) return st;
+  st = ensure_staging(h);
+  if (st != MC_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  MC_TRY(cudaMemcpyAsync(h->stage_bits, bitstream_host, bytes, cudaMemcpyHostToDevice, s));
+  h->launches_decode = 0;
+  Launches L{&h->launches_decode};
+  st = enqueue_decode(h, h->stage_bits, h->stage_pos, s, L);
+  if (st != MC_OK) return st;
+  k_flag_not_converged<<<(h->W + 255) / 256, 256, 0, s>>>(h->cg.done, h->W, h->d_status);
+  L.add(1);
+  MC_TRY(cudaMemcpyAsync(positions_out_host, h->stage_pos, sizeof(double) * 3ull * h->n * h->F,
+                         cudaMemcpyDeviceToHost, s));
+  MC_TRY(cudaGetLastError());
+  return read_status(h, s);
+}
+
+mesh_codec_status_t mesh_codec_get_stats(const mesh_codec_t* hc, mesh_codec_stats_t* st) {
+  if (!hc || !st) return MC_E_INVALID_ARG;
+  mesh_codec* h = const_cast<mesh_codec*>(hc);
+  std::memset(st, 0, sizeof(*st));
+  MC_TRY(cudaStreamSynchronize(h->last_stream));
+  for (int c = 0; c < 3; ++c) {
+    st->oi_sweeps[c] = h->oi_done[c];
+    st->oi_change[c] = h->oi_last_change[c];
+  }
+  st->launches_create = h->launches_create;
+  st->launches_encode = h->launches_encode;
+  st->launches_decode = h->launches_decode;
+  st->workspace_bytes = h->ws_bytes;
+  if (h->cg_columns > 0) {
+    std::vector<int32_t> it(h->cg_columns), dn(h->cg_columns);
+    std::vector<double> rr(h->cg_columns), bb(h->cg_columns);
+    MC_TRY(cudaMemcpy(it.data(), h->cg.iters, sizeof(int32_t) * it.size(), cudaMemcpyDeviceToHost));
+    MC_TRY(cudaMemcpy(dn.data(), h->cg.done, sizeof(int32_t) * dn.size(), cudaMemcpyDeviceToHost));
+    MC_TRY(cudaMemcpy(rr.data(), h->cg.rr, sizeof(double) * rr.size(), cudaMemcpyDeviceToHost));
+    MC_TRY(cudaMemcpy(bb.data(), h->cg.bb, sizeof(double) * bb.size(), cudaMemcpyDeviceToHost));
+    int mx = 0, mn = 1 << 30, nc = 0;
+    double sum = 0.0, res = 0.0;
+    for (int i = 0; i < h->cg_columns; ++i) {
+      mx = std::max(mx, it[i]);
+      mn = std::min(mn, it[i]);
+      sum += it[i];
+      if (dn[i] != 1) ++nc;
+      if (bb[i] > 0.0 && it[i] > 0) res = std::max(res, std::sqrt(rr[i] / bb[i]));
+    }
+    st->cg_iters_max = mx;
+    st->cg_iters_min = mn;
+    st->cg_iters_mean = sum / h->cg_columns;
+    st->cg_columns = h->cg_columns;
+    st->cg_not_converged = nc;
+    st->cg_rel_residual_max = res;
+  }
+  return MC_OK;
+}
+
+mesh_codec_status_t mesh_codec_buffer_size(const mesh_codec_t* h, int which, size_t* count,
+                                           size_t* elem_bytes) {
+  if (!h || !count || !elem_bytes) return MC_E_INVALID_ARG;
+  const size_t n = h->n, F = h->F, k = h->k, W = h->W;
+  switch (which) {
+    case MC_BUF_ROW_PTR: *count = n + 1; *elem_bytes = 4; break;
+    case MC_BUF_COL_IDX: *count = (size_t)h->nnz; *elem_bytes = 4; break;
+    case MC_BUF_DEGREE: *count = n; *elem_bytes = 4; break;
+    case MC_BUF_ANCHORS: *count = (size_t)h->n_c; *elem_bytes = 4; break;
+    case MC_BUF_DELTA: *count = n * W; *elem_bytes = 8; break;
+    case MC_BUF_BASIS: *count = 3 * F * k; *elem_bytes = 8; break;
+    case MC_BUF_RITZ: *count = 3 * k; *elem_bytes = 8; break;
+    case MC_BUF_COEFF: *count = 3 * k * n; *elem_bytes = 8; break;
+    case MC_BUF_START: *count = 3 * F * k; *elem_bytes = 8; break;
+    case MC_BUF_DELTA_REC: *count = n * W; *elem_bytes = 8; break;
+    case MC_BUF_CG_ITERS: *count = (size_t)h->cg_columns; *elem_bytes = 4; break;
+    default: return MC_E_INVALID_ARG;
+  }
+  return MC_OK;
+}
+
+mesh_codec_status_t mesh_codec_copy_buffer(const mesh_codec_t* h, int which, void* dst,
+                                           size_t count, void* stream) {
+  size_t cnt = 0, eb = 0;
+  mesh_codec_status_t st = mesh_codec_buffer_size(h, which, &cnt, &eb);
+  if (st != MC_OK) return st;
+  if (!dst || count != cnt) return MC_E_INVALID_ARG;
+  const void* src = nullptr;
+  switch (which) {
+    case MC_BUF_ROW_PTR: src = h->row_ptr; break;
+    case MC_BUF_COL_IDX: src = h->col_idx; break;
+    case MC_BUF_DEGREE: src = h->deg; break;
+    case MC_BUF_ANCHORS: src = h->anchors; break;
+    case MC_BUF_DELTA: src = h->D; break;
+    case MC_BUF_BASIS: src = h->U; break;
+    case MC_BUF_RITZ: src = h->theta; break;
+    case MC_BUF_COEFF: src = h->Cf; break;
+    case MC_BUF_START: src = h->Q0; break;
+    case MC_BUF_DELTA_REC: src = h->D; break;
+    case MC_BUF_CG_ITERS: src = h->cg.iters; break;
+  }
+  if (cnt == 0) return MC_OK;
+  MC_TRY(cudaMemcpyAsync(dst, src, cnt * eb, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return MC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,323 @@
+// Decoder solve (Eq. 12): the anchored least-squares problem
+//   min_X ||L X - delta~||^2 + ||P X - a^||^2
+// through its normal equations (L^T L + P^T P) X = L^T delta~ + P^T a^, solved
+// for all W columns at once by Jacobi-preconditioned conjugate gradients with
+// an independent step length per column (the paper's parallel
+// reconstruction, Section IV (v)).  The operator is applied as two Laplacian
+// sweeps, never assembled.
+//
+// Each iteration is six kernels over the [n][W] vectors:
+//   1. T = L P                          (SpMM over the adjacency)
+//   2. Q = L^T T + P^T P P, pAp partial (SpMM + dot, per row block)
+//   3. alpha = rz / pAp                 (per column, fixed-order reduction)
+//   4. X += alpha P, R -= alpha Q, partial rz = R.(D^-1 R), rr = R.R
+//   5. beta, convergence, active count  (per column, fixed-order reduction)
+//   6. P = D^-1 R + beta P
+// Dot products are reduced deterministically: per (row block, column)
+// partials in a fixed order, then one warp per column with a fixed shuffle
+// tree.  A converged column is frozen (alpha = beta = 0, no more updates),
+// so its result does not depend on the other columns.
+#include <algorithm>
+#include <math.h>
+
+#include "mc_internal.cuh"
+
+namespace mc {
+
+static constexpr int kCgThreads = 256;  // 32 columns x 8 row lanes
+
+CgGeom cg_geometry(int n, int W) {
+  CgGeom g{};
+  g.n = n;
+  g.W = W;
+  int col_tiles = (W + 31) / 32;
+  long long target = std::max(1, (152 * 16) / std::max(1, col_tiles));
+  int rpb = (int)((n + target - 1) / target);
+  rpb = std::max(8, (rpb + 7) / 8 * 8);
+  g.rows_per_block = rpb;
+  g.row_blocks = (n + rpb - 1) / rpb;
+  return g;
+}
+
+size_t cg_partials_elems(int n, int W) {
+  CgGeom g = cg_geometry(n, W);
+  return (size_t)g.row_blocks * W * 2;
+}
+
+// Combine the 8 row-lane partial sums of a column in fixed order and store
+// the CTA's partial for (row block, column).
+__device__ __forceinline__ void cta_col_partial(double v, double* sh, double* out, int col,
+                                                int W, bool valid) {
+  const int lane = threadIdx.x & 31, rl = threadIdx.x >> 5;
+  sh[rl * 32 + lane] = v;
+  __syncthreads();
+  if (rl == 0 && valid) {
+    double s = sh[lane];
+#pragma unroll
+    for (int r = 1; r < 8; ++r) s += sh[r * 32 + lane];
+    out[(long long)blockIdx.y * W + col] = s;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kCgThreads) k_cg_init(CgGeom g, const double* __restrict__ B,
+                                                        double* __restrict__ X,
+                                                        double* __restrict__ R,
+                                                        double* __restrict__ P,
+                                                        const double* __restrict__ inv_diag,
+                                                        double* __restrict__ partials) {
+  __shared__ double sh[256];
+  const int col = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int rl = threadIdx.x >> 5;
+  const bool valid = col < g.W;
+  const long long r0 = (long long)blockIdx.y * g.rows_per_block;
+  const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
+  double rz = 0.0, bb = 0.0;
+  if (valid) {
+    for (long long i = r0 + rl; i < r1; i += 8) {
+      long long e = i * g.W + col;
+      double b = B[e];
+      double z = b * inv_diag[i];
+      X[e] = 0.0;
+      R[e] = b;
+      P[e] = z;
+      rz = fma(b, z, rz);
+      bb = fma(b, b, bb);
+    }
+  }
+  const long long plane = (long long)g.row_blocks * g.W;
+  cta_col_partial(rz, sh, partials, col, g.W, valid);
+  cta_col_partial(bb, sh, partials + plane, col, g.W, valid);
+}
+
+// one warp per column: fixed-order sum of the row-block partials
+__device__ __forceinline__ double warp_col_sum(const double* part, int row_blocks, int W,
+                                               int col) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int b = lane; b < row_blocks; b += 32) s += part[(long long)b * W + col];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  return s;  // valid in lane 0
+}
+
+__global__ void k_cg_init_cols(CgGeom g, const double* __restrict__ partials, double* rz,
+                               double* bb, int32_t* done, int32_t* iters) {
+  const int col = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (col >= g.W) return;
+  const long long plane = (long long)g.row_blocks * g.W;
+  double a = warp_col_sum(partials, g.row_blocks, g.W, col);
+  double b = warp_col_sum(partials + plane, g.row_blocks, g.W, col);
+  if ((threadIdx.x & 31) == 0) {
+    rz[col] = a;
+    bb[col] = b;
+    done[col] = (b == 0.0) ? 1 : 0;
+    iters[col] = 0;
+  }
+}
+
+// T = L P for active columns
+__global__ void __launch_bounds__(kCgThreads) k_cg_L(CgGeom g, const int32_t* __restrict__ row_ptr,
+                                                     const int32_t* __restrict__ col_idx,
+                                                     const int32_t* __restrict__ deg,
+                                                     const double* __restrict__ inv_d, int kind,
+                                                     const double* __restrict__ P,
+                                                     double* __restrict__ T,
+                                                     const int32_t* __restrict__ done) {
+  const int col = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int rl = threadIdx.x >> 5;
+  if (col >= g.W || done[col]) return;
+  const long long r0 = (long long)blockIdx.y * g.rows_per_block;
+  const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
+  for (long long i = r0 + rl; i < r1; i += 8) {
+    int b = row_ptr[i], e = row_ptr[i + 1];
+    double acc = 0.0;
+    for (int p = b; p < e; ++p) acc += P[(long long)col_idx[p] * g.W + col];
+    double pi = P[i * g.W + col];
+    T[i * g.W + col] = (kind == 0) ? fma(-inv_d[i], acc, pi) : fma((double)deg[i], pi, -acc);
+  }
+}
+
+// Q = L^T T + [anchor] P and partial pAp
+__global__ void __launch_bounds__(kCgThreads) k_cg_LT(CgGeom g, const int32_t* __restrict__ row_ptr,
+                                                      const int32_t* __restrict__ col_idx,
+                                                      const int32_t* __restrict__ deg,
+                                                      const double* __restrict__ inv_d, int kind,
+                                                      const uint8_t* __restrict__ is_anchor,
+                                                      const double* __restrict__ T,
+                                                      const double* __restrict__ P,
+                                                      double* __restrict__ Q,
+                                                      const int32_t* __restrict__ done,
+                                                      double* __restrict__ partials) {
+  __shared__ double sh[256];
+  const int col = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int rl = threadIdx.x >> 5;
+  const bool valid = col < g.W && !done[col];
+  const long long r0 = (long long)blockIdx.y * g.rows_per_block;
+  const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
+  double pap = 0.0;
+  if (valid) {
+    for (long long j = r0 + rl; j < r1; j += 8) {
+      int b = row_ptr[j], e = row_ptr[j + 1];
+      double acc = 0.0;
+      if (kind == 0) {
+        for (int p = b; p < e; ++p) {
+          int i = col_idx[p];
+          acc = fma(inv_d[i], T[(long long)i * g.W + col], acc);
+        }
+      } else {
+        for (int p = b; p < e; ++p) acc += T[(long long)col_idx[p] * g.W + col];
+      }
+      double tj = T[j * g.W + col];
+      double q = (kind == 0) ? tj - acc : fma((double)deg[j], tj, -acc);
+      double pj = P[j * g.W + col];
+      if (is_anchor[j]) q += pj;
+      Q[j * g.W + col] = q;
+      pap = fma(pj, q, pap);
+    }
+  }
+  cta_col_partial(pap, sh, partials, col, g.W, col < g.W);
+}
+
+__global__ void k_cg_alpha(CgGeom g, const double* __restrict__ partials,
+                           const double* __restrict__ rz, double* alpha,
+                           const int32_t* __restrict__ done, int32_t* active) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *active = 0;
+  const int col = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (col >= g.W) return;
+  double pap = warp_col_sum(partials, g.row_blocks, g.W, col);
+  if ((threadIdx.x & 31) == 0) {
+    double a = 0.0;
+    if (!done[col] && pap > 0.0) a = rz[col] / pap;
+    alpha[col] = a;
+  }
+}
+
+__global__ void __launch_bounds__(kCgThreads) k_cg_update(CgGeom g, double* __restrict__ X,
+                                                          double* __restrict__ R,
+                                                          const double* __restrict__ P,
+                                                          const double* __restrict__ Q,
+                                                          const double* __restrict__ inv_diag,
+                                                          const double* __restrict__ alpha,
+                                                          const int32_t* __restrict__ done,
+                                                          double* __restrict__ partials) {
+  __shared__ double sh[256];
+  const int col = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int rl = threadIdx.x >> 5;
+  const bool valid = col < g.W && !done[col];
+  const long long r0 = (long long)blockIdx.y * g.rows_per_block;
+  const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
+  double rz = 0.0, rr = 0.0;
+  if (valid) {
+    const double a = alpha[col];
+    for (long long i = r0 + rl; i < r1; i += 8) {
+      long long e = i * g.W + col;
+      X[e] = fma(a, P[e], X[e]);
+      double r = fma(-a, Q[e], R[e]);
+      R[e] = r;
+      double z = r * inv_diag[i];
+      rz = fma(r, z, rz);
+      rr = fma(r, r, rr);
+    }
+  }
+  const long long plane = (long long)g.row_blocks * g.W;
+  cta_col_partial(rz, sh, partials, col, g.W, col < g.W);
+  cta_col_partial(rr, sh, partials + plane, col, g.W, col < g.W);
+}
+
+__global__ void k_cg_beta(CgGeom g, const double* __restrict__ partials, double* rz,
+                          double* rr_out, const double* __restrict__ bb, double* beta,
+                          int32_t* done, int32_t* iters, double rtol2, int max_iters,
+                          int32_t* active) {
+  const int col = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (col >= g.W) return;
+  const long long plane = (long long)g.row_blocks * g.W;
+  double rzn = warp_col_sum(partials, g.row_blocks, g.W, col);
+  double rr = warp_col_sum(partials + plane, g.row_blocks, g.W, col);
+  if ((threadIdx.x & 31) == 0) {
+    if (done[col]) {
+      beta[col] = 0.0;
+      return;
+    }
+    int it = iters[col] + 1;
+    iters[col] = it;
+    rr_out[col] = rr;
+    if (rr <= rtol2 * bb[col]) {
+      done[col] = 1;
+      beta[col] = 0.0;
+    } else if (it >= max_iters) {
+      done[col] = 2;  // cap reached
+      beta[col] = 0.0;
+    } else {
+      beta[col] = rzn / rz[col];
+      rz[col] = rzn;
+      atomicAdd(active, 1);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kCgThreads) k_cg_dir(CgGeom g, const double* __restrict__ R,
+                                                       double* __restrict__ P,
+                                                       const double* __restrict__ inv_diag,
+                                                       const double* __restrict__ beta,
+                                                       const int32_t* __restrict__ done) {
+  const int col = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int rl = threadIdx.x >> 5;
+  if (col >= g.W || done[col]) return;
+  const double b = beta[col];
+  const long long r0 = (long long)blockIdx.y * g.rows_per_block;
+  const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
+  for (long long i = r0 + rl; i < r1; i += 8) {
+    long long e = i * g.W + col;
+    P[e] = fma(b, P[e], R[e] * inv_diag[i]);
+  }
+}
+
+void cg_init(const CgGeom& g, const double* B, double* X, double* R, double* P,
+             const double* inv_diag, CgState& st, cudaStream_t s, Launches& L) {
+  dim3 grid((g.W + 31) / 32, g.row_blocks);
+  k_cg_init<<<grid, kCgThreads, 0, s>>>(g, B, X, R, P, inv_diag, st.partials);
+  k_cg_init_cols<<<(g.W + 7) / 8, 256, 0, s>>>(g, st.partials, st.rz, st.bb, st.done, st.iters);
+  L.add(2);
+}
+
+void cg_iteration(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx,
+                  const int32_t* deg, const double* inv_d, const uint8_t* is_anchor,
+                  const double* inv_diag, int kind, double* X, double* R, double* P, double* T,
+                  double* Q, double rtol, int max_iters, CgState& st, cudaStream_t s,
+                  Launches& L) {
+  dim3 grid((g.W + 31) / 32, g.row_blocks);
+  dim3 cgrid((g.W + 7) / 8);
+  k_cg_L<<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, P, T, st.done);
+  k_cg_LT<<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, is_anchor, T, P, Q,
+                                       st.done, st.partials);
+  k_cg_alpha<<<cgrid, 256, 0, s>>>(g, st.partials, st.rz, st.alpha, st.done, st.active);
+  k_cg_update<<<grid, kCgThreads, 0, s>>>(g, X, R, P, Q, inv_diag, st.alpha, st.done,
+                                           st.partials);
+  k_cg_beta<<<cgrid, 256, 0, s>>>(g, st.partials, st.rz, st.rr, st.bb, st.beta, st.done,
+                                  st.iters, rtol * rtol, max_iters, st.active);
+  k_cg_dir<<<grid, kCgThreads, 0, s>>>(g, R, P, inv_diag, st.beta, st.done);
+  L.add(6);
+}
+
+// B[anchor a][coord_cols + f] += Ahat[a][f]   (P^T a^ for one coordinate block)
+__global__ void k_scatter_anchor_rhs(double* B, const double* __restrict__ Ahat,
+                                     const int32_t* __restrict__ anchors, int n_c, int F, int W,
+                                     int coord_cols) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n_c * F;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long a = e / F, f = e % F;
+    B[(long long)anchors[a] * W + coord_cols + f] += Ahat[e];
+  }
+}
+
+void scatter_anchor_rhs(double* B, const double* Ahat, const int32_t* anchors, int n_c, int F,
+                        int W, int coord_cols, cudaStream_t s, Launches& L) {
+  if (n_c <= 0) return;
+  long long tot = (long long)n_c * F;
+  int grid = (int)std::min<long long>((tot + 255) / 256, 1024);
+  k_scatter_anchor_rhs<<<grid, 256, 0, s>>>(B, Ahat, anchors, n_c, F, W, coord_cols);
+  L.add(1);
+}
+
+}  // namespace mc

@@ -1,0 +1,168 @@
+// Internal declarations shared by the codec's translation units.
+//
+// Device data layout (one handle, one connectivity):
+//   vertex-major frame matrices  [n][W], W = 3F, column c*F + f holds
+//   coordinate c of frame f; a vertex's whole trajectory (all three
+//   coordinates) is one contiguous row, so the Laplacian's neighbour gathers
+//   read contiguous rows and the per-coordinate matrix A_c^T (n x F) is a
+//   strided view.
+//   CSR adjacency without the diagonal (row_ptr [n+1], col_idx [nnz], deg [n]).
+//   Small dense matrices per coordinate: [3][F][k] row-major.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/mesh_codec.h"
+
+namespace mc {
+
+// status bits set by device code (atomicOr into Handle::d_status)
+enum : uint32_t {
+  ST_BAD_INDEX = 1u << 0,
+  ST_DEGENERATE = 1u << 1,
+  ST_ISOLATED = 1u << 2,
+  ST_CHOL_BREAKDOWN = 1u << 3,
+  ST_BAD_ANCHORS = 1u << 4,
+  ST_NOT_CONVERGED = 1u << 5,
+  ST_BITSTREAM = 1u << 6,
+};
+
+// splitmix64 (Steele, Lea, Flood 2014): output i of the generator seeded with s.
+__host__ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t s, uint64_t i) {
+  uint64_t z = s + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+// The codec's salts: part of its definition ("anchors!", "basis_00").
+constexpr uint64_t kAnchorSalt = 0x616E63686F727321ull;
+constexpr uint64_t kBasisSalt = 0x62617369735F3030ull;
+
+struct Launches {
+  uint64_t* counter = nullptr;
+  void add(uint64_t k = 1) { if (counter) *counter += k; }
+};
+
+// ---------------------------------------------------------------- graph
+struct CsrBuildTmp {
+  int32_t* raw_deg;     // [n]
+  int32_t* raw_off;     // [n+1]
+  int32_t* cursor;      // [n]
+  int32_t* raw_col;     // [6T]
+  int32_t* scan_tmp;    // scan scratch
+};
+size_t scan_tmp_elems(int n);
+void exclusive_scan_i32(const int32_t* in, int32_t* out, int n, int32_t* tmp,
+                        cudaStream_t s, Launches& L);  // out has n+1 entries
+void build_csr(const int32_t* tris, int T, int n, CsrBuildTmp& t, int32_t* row_ptr,
+               int32_t* col_idx_or_null, int32_t* deg, uint32_t* status, cudaStream_t s,
+               Launches& L);
+void compact_csr(const CsrBuildTmp& t, const int32_t* row_ptr, int32_t* col_idx, int n,
+                 cudaStream_t s, Launches& L);
+void select_anchors(int n, int n_c, uint64_t seed, int32_t* anchors, cudaStream_t s,
+                    Launches& L);
+void check_anchors(const int32_t* anchors, int n_c, int n, uint32_t* status, cudaStream_t s,
+                   Launches& L);
+void vertex_scalars_marked(const int32_t* row_ptr, const int32_t* col_idx, const int32_t* deg,
+                           const uint8_t* is_anchor, int n, int kind, double* inv_d,
+                           double* inv_diag_m, cudaStream_t s, Launches& L);
+// delta = L X over W columns (Eq. 3 sum-then-divide / Eq. 4), bit-exact order
+void laplacian_rows(const int32_t* row_ptr, const int32_t* col_idx, const int32_t* deg,
+                    const double* X, double* Y, int n, int W, int kind, cudaStream_t s,
+                    Launches& L);
+// B = L^T Y (+ anchors scattered by a separate call)
+void laplacian_t_rows(const int32_t* row_ptr, const int32_t* col_idx, const int32_t* deg,
+                      const double* inv_d, const double* Y, double* B, int n, int W, int kind,
+                      cudaStream_t s, Launches& L);
+
+// ---------------------------------------------------------------- layout
+void frames_to_vertex_major(const double* pos, double* X, int F, int n, cudaStream_t s,
+                            Launches& L);
+void vertex_major_to_frames(const double* X, double* pos, int F, int n, cudaStream_t s,
+                            Launches& L);
+
+// ---------------------------------------------------------------- dense FP64
+struct Strided {  // element (r, c) at p[r*s0 + c*s1] + batch*sb
+  const double* p;
+  long long s0, s1, sb;
+};
+struct StridedOut {
+  double* p;
+  long long s0, s1, sb;
+};
+// C(b) = A(b) B(b) for b < batch, (M x K)(K x N); split-K into `splits` partial
+// sums reduced in fixed order (partials: splits*batch*M*N doubles)
+void dgemm(int M, int N, int K, int batch, Strided A, Strided B, StridedOut C, int splits,
+           double* partials, cudaStream_t s, Launches& L);
+void gen_start_basis(double* Z, int F, int k, uint64_t seed, cudaStream_t s, Launches& L);
+// Q = qr(Z) by shifted CholeskyQR3, batch of 3, in place on Z (Z -> Q)
+void cholqr3(double* Z, int F, int k, double* G, double* R, double* partials, int splits,
+             uint32_t* status, cudaStream_t s, Launches& L);
+void oi_change(const double* Qold, const double* Qnew, int F, int k, double* work,
+               double* change, cudaStream_t s, Launches& L);
+// eigen-decomposition of H (3 x k x k): V (k x k, columns = eigenvectors,
+// sorted descending), theta (k)
+void jacobi_eig(const double* H, double* V, double* theta, int k, cudaStream_t s,
+                Launches& L);
+void sign_rule(double* U, int F, int k, cudaStream_t s, Launches& L);
+
+// ---------------------------------------------------------------- quantizer
+struct Section {     // one coded section of the bitstream
+  int bits;          // 0 = raw float64
+  long long count;   // symbols
+  long long offset;  // byte offset of the section in the stream
+};
+// lo/hi of row r of batch b: min/max over cols of A[b*s_batch + r*s_row + c*s_col],
+// written to lo[b*out_sb + r] / hi[b*out_sb + r] (exact, order-free)
+void minmax_rows_out(const double* A, long long rows, long long cols, long long s_row,
+                     long long s_col, int batch, long long s_batch, double* lo, double* hi,
+                     long long out_sb, cudaStream_t s, Launches& L);
+// per coordinate c: min/max over all anchor values -> lo[c*out_sb], hi[c*out_sb]
+void anchor_minmax_out(const double* X, const int32_t* anchors, int n_c, int F, double* lo,
+                       double* hi, long long out_sb, cudaStream_t s, Launches& L);
+
+struct EncodeLayout {
+  int n, F, k, n_c, cb, db, ab, kind;
+  long long total;
+  long long anchors_off;
+  long long coord_off[3];  // start of each coordinate block (its params)
+  Section dict[3], coef[3], anch[3];
+};
+EncodeLayout make_layout(int n, int F, int k, int n_c, int cb, int db, int ab, int kind);
+void write_header(uint8_t* out, const EncodeLayout& lay, const int32_t* anchors,
+                  const double* qparams /*[3][4k+2]*/, cudaStream_t s, Launches& L);
+void quant_pack_sections(uint8_t* out, const EncodeLayout& lay, const double* U,
+                         const double* C, const double* X, const int32_t* anchors,
+                         const double* qparams, cudaStream_t s, Launches& L);
+void unpack_sections(const uint8_t* in, const EncodeLayout& lay, double* Udeq, double* Cdeq,
+                     double* Ahat, int32_t* anchors, double* unused, uint32_t* status,
+                     cudaStream_t s, Launches& L);
+
+// ---------------------------------------------------------------- CG
+struct CgState {
+  double *rz, *rr, *bb, *pap, *alpha, *beta;  // [W]
+  int32_t *done, *iters;                       // [W]
+  double* partials;                            // [row_blocks * W * 2]
+  int32_t* active;                             // [1] number of active columns
+  int32_t* all_done;                           // [1]
+};
+struct CgGeom {
+  int n, W, row_blocks, rows_per_block;
+};
+CgGeom cg_geometry(int n, int W);
+size_t cg_partials_elems(int n, int W);
+void cg_init(const CgGeom& g, const double* B, double* X, double* R, double* P,
+             const double* inv_diag, CgState& st, cudaStream_t s, Launches& L);
+void cg_iteration(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx,
+                  const int32_t* deg, const double* inv_d, const uint8_t* is_anchor,
+                  const double* inv_diag, int kind, double* X, double* R, double* P, double* T,
+                  double* Q, double rtol, int max_iters, CgState& st, cudaStream_t s,
+                  Launches& L);
+void scatter_anchor_rhs(double* B, const double* Ahat, const int32_t* anchors, int n_c, int F,
+                        int W, int coord_cols, cudaStream_t s, Launches& L);
+void mark_anchors(const int32_t* anchors, int n_c, uint8_t* is_anchor, cudaStream_t s,
+                  Launches& L);
+
+}  // namespace mc
