@@ -26,8 +26,10 @@ problem of Eq. 12,  min_X ||L X - delta~_c||^2 + ||P X - a^_c||^2  with P the
 rows of the identity at N and unit weights, through its normal equations
 (L^T L + P^T P) X = L^T delta~_c + P^T a^_c for all F frames at once (the
 paper's parallel reconstruction "PCA+qp", Section IV (v)).  The oracle
-solves them directly (sparse LU, SuperLU through scipy) and applies one
-step of iterative refinement.  Eq. 12 as printed stacks an F x n block on
+solves them with sparse LU (SuperLU through scipy) of the assembled matrix,
+then refines the result with residuals of the unassembled operator
+L^T (L X) + P^T P X computed in extended precision, so that it returns the
+binary64 rounding of the exact solution.  Eq. 12 as printed stacks an F x n block on
 an n_c x F block; reading it as the least-squares problem above is the
 only dimensionally consistent form.
 
@@ -218,16 +220,64 @@ def normal_matrix(row_ptr, col_idx, deg, anchors, kind=0):
     return (L.T @ L + P.T @ P).tocsc(), L, P
 
 
-def solve_anchored_ls(row_ptr, col_idx, deg, anchors, delta_t, a_hat, kind=0, refine=1):
-    """X minimising ||L X - delta_t||^2 + ||P X - a_hat||^2 (Eq. 12)."""
+def normal_operator_ext(row_ptr, col_idx, deg, anchors, kind=0):
+    """X -> (L^T L + P^T P) X applied as two Laplacian sweeps in extended
+    precision (numpy longdouble), with the exact division by d_i of Eq. 3.
+
+    Forming L^T L in binary64 perturbs the operator's smallest eigenvalues
+    enough to move the least-squares solution by ~1e-10 relative; the
+    unassembled operator in extended precision does not."""
+    n = row_ptr.shape[0] - 1
+    ext = np.longdouble
+    rows = np.repeat(np.arange(n), np.diff(row_ptr.astype(np.int64)))
+    C = sp.csr_matrix((np.ones(rows.shape[0], dtype=ext), (rows, col_idx.astype(np.int64))),
+                      shape=(n, n))
+    d = deg.astype(ext)[:, None]
+    is_anchor = np.zeros(n, dtype=bool)
+    is_anchor[anchors] = True
+
+    def apply(X):
+        X = np.asarray(X).astype(ext)
+        if kind == 0:
+            Y = X - (C @ X) / d
+            Z = Y - C @ (Y / d)
+        else:
+            Y = d * X - C @ X
+            Z = d * Y - C @ Y
+        Z[is_anchor] += X[is_anchor]
+        return Z
+
+    return apply
+
+
+def _refined_solve(lu, op_ext, b, max_steps=8):
+    """Sparse LU as the approximate solver, then iterative refinement with
+    residuals b - (L^T L + P^T P) X computed in extended precision, until the
+    correction is below one unit in the last place of X."""
+    X = lu.solve(b)
+    b_ext = b.astype(np.longdouble)
+    for _ in range(max_steps):
+        r = (b_ext - op_ext(X)).astype(np.float64)
+        dx = lu.solve(r)
+        X = X + dx
+        if np.abs(dx).max() <= 2.0 ** -52 * np.abs(X).max():
+            break
+    return X
+
+
+def _factor(M):
+    return spla.splu(M, permc_spec="MMD_AT_PLUS_A", diag_pivot_thresh=0.0,
+                     options={"SymmetricMode": True})
+
+
+def solve_anchored_ls(row_ptr, col_idx, deg, anchors, delta_t, a_hat, kind=0):
+    """X minimising ||L X - delta_t||^2 + ||P X - a_hat||^2 (Eq. 12), through
+    the normal equations (L^T L + P^T P) X = L^T delta_t + P^T a_hat."""
     M, L, P = normal_matrix(row_ptr, col_idx, deg, anchors, kind)
     b = graph.apply_laplacian_transpose(row_ptr, col_idx, deg, delta_t, kind)
     b[anchors] += a_hat
-    lu = spla.splu(M, permc_spec="MMD_AT_PLUS_A", diag_pivot_thresh=0.0,
-                   options={"SymmetricMode": True})
-    X = lu.solve(b)
-    for _ in range(refine):
-        X = X + lu.solve(b - M @ X)
+    op = normal_operator_ext(row_ptr, col_idx, deg, anchors, kind)
+    X = _refined_solve(_factor(M), op, b)
     return X, b, M
 
 
@@ -237,13 +287,11 @@ def decode(blob, tris):
     row_ptr, col_idx, deg = graph.build_adjacency(tris, n)
     out = np.empty((F, n, 3), dtype=np.float64)
     M, L, P = normal_matrix(row_ptr, col_idx, deg, d["anchors"], d["kind"])
-    lu = spla.splu(M, permc_spec="MMD_AT_PLUS_A", diag_pivot_thresh=0.0,
-                   options={"SymmetricMode": True})
+    lu = _factor(M)
+    op = normal_operator_ext(row_ptr, col_idx, deg, d["anchors"], d["kind"])
     for c in range(3):
         delta_t = (d["U"][c] @ d["C"][c]).T                          # n x F (Eq. 11)
         b = graph.apply_laplacian_transpose(row_ptr, col_idx, deg, delta_t, d["kind"])
         b[d["anchors"]] += d["a"][c]
-        X = lu.solve(b)
-        X = X + lu.solve(b - M @ X)
-        out[:, :, c] = X.T
+        out[:, :, c] = _refined_solve(lu, op, b).T
     return out
