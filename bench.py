@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark of the dynamic-mesh codec: encode + decode vertex-frames/s.
+
+One step = one encode (delta coordinates, orthogonal iterations, projection,
+quantization and packing) plus one decode (unpacking, back-projection,
+right-hand sides, anchored least-squares CG solve, output) of one synthetic
+sequence, with the input already resident in device memory.  The workload is
+the 20 000-vertex torus sequence (F = 256 frames, k = 32, 12-bit
+coefficients, 16-bit dictionary and anchors, 50 anchors) in the FP64 mode.
+
+Prints ONE JSON line (rank 0).  Under torchrun each rank runs an independent
+replica on its own GPU (the codec does not shard a sequence); `value` is the
+vertex-frames of all ranks divided by the slowest rank's time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "encode+decode vertex-frames/s at fixed NMSE vs FP64 oracle; % of HBM/TC roofline"
+UNIT = "vertex-frames/s"
+WORKLOAD = "torus200x100_F256_k32"
+SWEEPS = 30
+NMSE_RTOL = 1e-9
+# FP64 peak of a GB300: 152 SMs x 2 FP64 FMA per SM per clock x 2 flop x 2.07 GHz
+# (the nominal 1.25 TFLOP/s divided by the SM count and the maximum SM clock
+# gives 3.97 flop per SM per clock).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+L2_FLUSH_BYTES = 256 << 20
+CPU_SAMPLE_FRAMES = 64       # cpu_baseline: first 64 frames of the same sequence
+REF_SAMPLE_FRAMES = 32       # --impl reference: per-step sample
+
+
+# ---------------------------------------------------------------- helpers
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def nmse_reference(workload):
+    path = os.path.join(ROOT, "tests", "golden", "nmse_reference.txt")
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if parts and not line.startswith("#") and parts[0] == workload:
+                return int(parts[1]), float(parts[2])
+    raise KeyError(workload)
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def aggregate(vf_local, seconds_local, world, dist=None):
+    """Whole-job throughput: sum of vertex-frames over ranks / max time."""
+    if world > 1 and dist is not None:
+        import torch
+        t = torch.tensor([float(seconds_local)], dtype=torch.float64)
+        v = torch.tensor([float(vf_local)], dtype=torch.float64)
+        if dist.get_backend() == "nccl":
+            t, v = t.cuda(), v.cuda()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(v, op=dist.ReduceOp.SUM)
+        return v.item() / t.item(), t.item()
+    return vf_local / seconds_local, seconds_local
+
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, max clock, throttle reasons) while the
+    timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        self.uuid = device_uuid
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [l.strip().split(", ") for l in self.file.read().splitlines() if l.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_work(name, n, W_active, nnz, n_c):
+    """Algorithmic FP64 flops and bytes of one launch of a decoder CG kernel
+    (FMA = 2 flop), for W_active active columns over n vertices."""
+    e = n * W_active                      # vertex-column entries
+    dbar = nnz / n
+    csr = 4 * (n + 1) + 4 * nnz
+    if name == "k_cg_L":
+        return e * (dbar + 2), e * 16 + csr + 8 * n
+    if name == "k_cg_LT":
+        return e * (2 * dbar + 3) + n_c * W_active, e * 24 + csr + 9 * n
+    if name == "k_cg_update":
+        return e * 9, e * 48 + 8 * n
+    if name == "k_cg_dir":
+        return e * 3, e * 24 + 8 * n
+    return 0.0, 0.0
+
+
+def roofline(profile, stats, n, W, nnz, n_c, peaks):
+    """Dominant CG kernel's achieved FP64 rate against the FP64 peak."""
+    best, best_ms = None, -1.0
+    shares = {}
+    total = sum(ms for (_, ms) in profile.values())
+    for name, (launches, ms) in profile.items():
+        if launches:
+            shares[name] = ms / total if total else 0.0
+            if ms > best_ms:
+                best, best_ms = name, ms
+    launches, ms = profile[best]
+    mean_s = ms / launches / 1e3
+    W_active = W * stats["cg_iters_mean"] / max(1, stats["cg_iters_max"])
+    flops, nbytes = kernel_work(best, n, W_active, nnz, n_c)
+    achieved = flops / mean_s / 1e12
+    return {
+        "kernel": best, "bound": "alu", "achieved": round(achieved, 4),
+        "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+        "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+        "algorithmic_bytes": int(nbytes), "mean_launch_ms": round(mean_s * 1e3, 5),
+        "hbm_GBps_at_algorithmic_bytes": round(nbytes / mean_s / 1e9, 1),
+        "hbm_peak_GBps": peaks.get("hbm_gbs"),
+        "launches_timed": launches, "time_share": {k: round(v, 4) for k, v in shares.items()},
+        "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+    }
+
+
+# ---------------------------------------------------------------- oracle legs
+def oracle_sample(frames, repeats=1):
+    """Time the FP64 oracle (single-threaded BLAS) on the first `frames`
+    frames of the workload's sequence, in a child process."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1",
+               MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    code = (
+        "import sys, time, json; sys.path.insert(0, %r)\n"
+        "from synth import make_sequence, config_spec\n"
+        "from oracle import codec, metrics\n"
+        "spec = config_spec(%r); tris, pos = make_sequence(spec); pos = pos[:%d].copy()\n"
+        "p = codec.Params(n_frames=pos.shape[0], rank=min(spec.rank, pos.shape[0]),"
+        " n_anchors=spec.n_anchors, seed=spec.seed, oi_sweeps=%d)\n"
+        "out = []\n"
+        "for _ in range(%d):\n"
+        "    t0 = time.perf_counter(); blob = codec.encode(tris, pos, p)\n"
+        "    t1 = time.perf_counter(); rec = codec.decode(blob, tris); t2 = time.perf_counter()\n"
+        "    out.append([t1 - t0, t2 - t1])\n"
+        "print(json.dumps({'n': pos.shape[1], 'F': pos.shape[0], 'times': out,"
+        " 'nmse': metrics.nmse(pos, rec)}))\n"
+    ) % (ROOT, WORKLOAD, frames, SWEEPS, repeats)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline():
+    res = oracle_sample(CPU_SAMPLE_FRAMES, repeats=1)
+    enc, dec = res["times"][0]
+    vf = res["n"] * res["F"]
+    return {"value": vf / (enc + dec), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{WORKLOAD} first {res['F']} frames (n={res['n']}), one encode+decode, "
+                       f"single-threaded numpy/scipy, encode {enc:.2f} s + decode {dec:.2f} s")}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_sample(REF_SAMPLE_FRAMES, repeats=1)
+    t0 = time.perf_counter()
+    res = oracle_sample(REF_SAMPLE_FRAMES, repeats=args.steps)
+    wall = time.perf_counter() - t0
+    secs = sum(a + b for a, b in res["times"])
+    vf = res["n"] * res["F"] * args.steps
+    value = vf / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD} (first {res['F']} frames per step)",
+                   "n": res["n"], "F": res["F"], "sweeps": SWEEPS},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{WORKLOAD} first {res['F']} frames, single-threaded, "
+                                   f"{args.steps} encode+decode passes ({wall:.1f} s wall)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "nmse": res["nmse"],
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from oracle import metrics   # NMSE of the result, computed on the host
+    from paper_2111_10105_gb300 import MeshCodec
+    from synth import make_sequence, config_spec
+
+    world, rank, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    spec = config_spec(WORKLOAD)
+    tris, pos = make_sequence(spec)
+    F, n = pos.shape[0], pos.shape[1]
+    kw = dict(n_frames=F, rank=spec.rank, n_anchors=spec.n_anchors, seed=spec.seed,
+              coeff_bits=spec.coeff_bits, dict_bits=spec.dict_bits,
+              anchor_bits=spec.anchor_bits, oi_sweeps=SWEEPS)
+    mc = MeshCodec(tris, n, **kw)
+    pos_dev = torch.from_numpy(pos).to(dev)
+    bits = torch.empty(mc.stream_bytes, dtype=torch.uint8, device=dev)
+    rec = torch.empty_like(pos_dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        mc.encode(pos_dev, out=bits, stream=stream)
+        mc.decode(bits, out=rec, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    stats = mc.stats()
+    mc.set_profiling(16)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    total_ms = 0.0
+    launches = 0
+    for _ in range(args.steps):
+        flush.zero_()                                   # L2 flush, not timed
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        st = mc.stats()
+        launches += st["launches_encode"] + st["launches_decode"]
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    if dist is not None:
+        dist.barrier()
+    profile = mc.profile()
+    mc.set_profiling(0)
+    stats = mc.stats()
+    vf_local = n * F * args.steps
+    value, seconds = aggregate(vf_local, total_ms / 1e3, world, dist)
+
+    # NMSE of this run's reconstruction vs the oracle's stored value
+    sweeps_ref, nmse_ref = nmse_reference(WORKLOAD)
+    nmse = metrics.nmse(pos, rec.cpu().numpy())
+    nmse_ok = sweeps_ref == SWEEPS and abs(nmse - nmse_ref) <= NMSE_RTOL * nmse_ref
+
+    # end to end through the host-buffer entry points (pinned host memory)
+    pos_h = torch.from_numpy(pos).pin_memory()
+    bits_h = torch.empty(mc.stream_bytes, dtype=torch.uint8).pin_memory()
+    rec_h = torch.empty((F, n, 3), dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        mc.encode_host(pos_h, out=bits_h, stream=stream)
+        mc.decode_host(bits_h, out=rec_h, stream=stream)
+    e2e_s = time.perf_counter() - t0
+    e2e_value, _ = aggregate(n * F * e2e_steps, e2e_s, world, dist)
+    nbytes_pos = pos.nbytes
+
+    peaks = measured_peaks()
+    nnz = int(mc.buffer(1).numel())
+    rl = roofline(profile, stats, n, 3 * F, nnz, spec.n_anchors, peaks)
+
+    out = None
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": seconds * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "mesh": "closed torus grid 200x100", "n": n, "F": F,
+                       "k": spec.rank, "anchors": spec.n_anchors,
+                       "bits": [spec.coeff_bits, spec.dict_bits, spec.anchor_bits],
+                       "oi_sweeps": SWEEPS, "cg_rtol": 1e-14, "precision": "fp64",
+                       "decode_columns": 3 * F, "l2": "flushed (256 MiB write) before every step",
+                       "parallelism": f"replicas x{world}"},
+            "nmse": nmse, "nmse_oracle": nmse_ref, "nmse_within_1e-9": bool(nmse_ok),
+            "cg_iters_max": stats["cg_iters_max"], "cg_iters_mean": stats["cg_iters_mean"],
+            "roofline": rl,
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": nbytes_pos + mc.stream_bytes,
+                    "d2h_bytes_per_step": mc.stream_bytes + nbytes_pos,
+                    "steps": e2e_steps},
+            "gpu_launches": launches,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out), flush=True)
+    mc.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -206,6 +206,22 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_buffer_size(const mesh_codec_t* h,
 MESH_CODEC_API mesh_codec_status_t mesh_codec_copy_buffer(const mesh_codec_t* h, int which,
                                            void* dst, size_t count, void* stream);
 
+/* Kernel timing.  With `every` > 0, each decode records CUDA events on its
+ * stream around the kernels of every `every`-th CG iteration and adds their
+ * durations to per-kernel totals; 0 turns it off.  Either call resets the
+ * totals.  mesh_codec_get_profile synchronises the handle's last stream. */
+#define MESH_CODEC_PROF_KERNELS 8
+typedef struct mesh_codec_profile {
+    int32_t n_kernels;
+    int32_t reserved;
+    char name[MESH_CODEC_PROF_KERNELS][32];
+    int64_t launches_timed[MESH_CODEC_PROF_KERNELS];
+    double total_ms[MESH_CODEC_PROF_KERNELS];
+} mesh_codec_profile_t;
+MESH_CODEC_API mesh_codec_status_t mesh_codec_set_profiling(mesh_codec_t* h, int every);
+MESH_CODEC_API mesh_codec_status_t mesh_codec_get_profile(const mesh_codec_t* h,
+                                                          mesh_codec_profile_t* out);
+
 /* Frees the handle and its workspace (synchronises the device first).
  * NULL is accepted. */
 MESH_CODEC_API void mesh_codec_destroy(mesh_codec_t* h);

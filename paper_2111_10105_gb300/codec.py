@@ -62,6 +62,14 @@ class Stats(ctypes.Structure):
         return out
 
 
+class Profile(ctypes.Structure):
+    _fields_ = [
+        ("n_kernels", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("name", (ctypes.c_char * 32) * 8), ("launches_timed", ctypes.c_int64 * 8),
+        ("total_ms", ctypes.c_double * 8),
+    ]
+
+
 class MeshCodecError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -88,6 +96,8 @@ _SIGS = {
     "mesh_codec_buffer_size": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t),
                                               ctypes.POINTER(ctypes.c_size_t)]),
     "mesh_codec_copy_buffer": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t, _P]),
+    "mesh_codec_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
+    "mesh_codec_get_profile": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "mesh_codec_destroy": (None, [_P]),
 }
 
@@ -234,6 +244,18 @@ class MeshCodec:
         s = Stats()
         _check(self._lib.mesh_codec_get_stats(self._h, ctypes.byref(s)), "mesh_codec_get_stats")
         return s.as_dict()
+
+    def set_profiling(self, every):
+        """Time the decoder's CG kernels with CUDA events on every `every`-th
+        iteration (0 = off); resets the totals."""
+        _check(self._lib.mesh_codec_set_profiling(self._h, int(every)), "mesh_codec_set_profiling")
+
+    def profile(self):
+        """{kernel name: (launches timed, total ms)}"""
+        p = Profile()
+        _check(self._lib.mesh_codec_get_profile(self._h, ctypes.byref(p)), "mesh_codec_get_profile")
+        return {bytes(p.name[i]).split(b"\0")[0].decode(): (p.launches_timed[i], p.total_ms[i])
+                for i in range(p.n_kernels)}
 
     def buffer(self, which, stream=None):
         torch = _torch()

@@ -52,6 +52,12 @@ struct mesh_codec {
   int oi_done[3] = {0, 0, 0};
   double oi_last_change[3] = {0, 0, 0};
   int cg_columns = 0;
+  // kernel timing (mesh_codec_set_profiling)
+  int prof_every = 0;
+  std::vector<cudaEvent_t> prof_events;   // groups of kCgKernels + 1
+  size_t prof_used = 0;                    // groups recorded in the current decode
+  int64_t prof_launches[MESH_CODEC_PROF_KERNELS] = {0};
+  double prof_ms[MESH_CODEC_PROF_KERNELS] = {0};
 };
 
 namespace {
@@ -227,6 +233,7 @@ void mesh_codec_destroy(mesh_codec_t* h) {
   if (h->h_active) cudaFreeHost(h->h_active);
   if (h->h_header) cudaFreeHost(h->h_header);
   if (h->h_chg) cudaFreeHost(h->h_chg);
+  for (cudaEvent_t e : h->prof_events) cudaEventDestroy(e);
   delete h;
 }
 
@@ -448,6 +455,36 @@ static mesh_codec_status_t check_header(mesh_codec* h, const uint8_t* hdr, size_
   return MC_OK;
 }
 
+// events for CG iteration `it` when profiling samples it, else null
+static cudaEvent_t* prof_group(mesh_codec* h, int it) {
+  if (h->prof_every <= 0 || it % h->prof_every != 0) return nullptr;
+  const size_t G = kCgKernels + 1;
+  if ((h->prof_used + 1) * G > h->prof_events.size()) {
+    for (size_t i = 0; i < G; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      h->prof_events.push_back(e);
+    }
+  }
+  return &h->prof_events[(h->prof_used++) * G];
+}
+
+// after the decode's final synchronisation: fold the recorded groups into totals
+static void prof_collect(mesh_codec* h) {
+  const size_t G = kCgKernels + 1;
+  for (size_t g = 0; g < h->prof_used; ++g) {
+    for (int k = 0; k < kCgKernels; ++k) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, h->prof_events[g * G + k], h->prof_events[g * G + k + 1]) ==
+          cudaSuccess) {
+        h->prof_ms[k] += ms;
+        h->prof_launches[k] += 1;
+      }
+    }
+  }
+  h->prof_used = 0;
+}
+
 static mesh_codec_status_t enqueue_decode(mesh_codec* h, const uint8_t* in, double* out,
                                           cudaStream_t s, Launches& L) {
   const int n = h->n, F = h->F, k = h->k, W = h->W;
@@ -477,7 +514,7 @@ static mesh_codec_status_t enqueue_decode(mesh_codec* h, const uint8_t* in, doub
     for (int j = 0; j < m; ++j)
       cg_iteration(h->geom, h->row_ptr, h->col_idx, h->deg, h->inv_d, h->is_anchor, h->inv_diag,
                    h->kind, h->X, h->R, h->P, h->Tv, h->Qv, h->p.cg_rtol, h->p.cg_max_iters, h->cg,
-                   s, L);
+                   s, L, prof_group(h, it + j));
     it += m;
     MC_TRY(cudaMemcpyAsync(h->h_active, h->cg.active, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     MC_TRY(cudaStreamSynchronize(s));
@@ -511,7 +548,9 @@ mesh_codec_status_t mesh_codec_decode(mesh_codec_t* h, const uint8_t* bitstream,
   k_flag_not_converged<<<(h->W + 255) / 256, 256, 0, s>>>(h->cg.done, h->W, h->d_status);
   L.add(1);
   MC_TRY(cudaGetLastError());
-  return read_status(h, s);
+  st = read_status(h, s);
+  prof_collect(h);
+  return st;
 }
 
 static mesh_codec_status_t ensure_staging(mesh_codec* h) {
@@ -562,7 +601,34 @@ mesh_codec_status_t mesh_codec_decode_host(mesh_codec_t* h, const uint8_t* bitst
   MC_TRY(cudaMemcpyAsync(positions_out_host, h->stage_pos, sizeof(double) * 3ull * h->n * h->F,
                          cudaMemcpyDeviceToHost, s));
   MC_TRY(cudaGetLastError());
-  return read_status(h, s);
+  st = read_status(h, s);
+  prof_collect(h);
+  return st;
+}
+
+mesh_codec_status_t mesh_codec_set_profiling(mesh_codec_t* h, int every) {
+  if (!h || every < 0) return MC_E_INVALID_ARG;
+  h->prof_every = every;
+  h->prof_used = 0;
+  for (int k = 0; k < MESH_CODEC_PROF_KERNELS; ++k) {
+    h->prof_ms[k] = 0.0;
+    h->prof_launches[k] = 0;
+  }
+  return MC_OK;
+}
+
+mesh_codec_status_t mesh_codec_get_profile(const mesh_codec_t* hc, mesh_codec_profile_t* out) {
+  if (!hc || !out) return MC_E_INVALID_ARG;
+  mesh_codec* h = const_cast<mesh_codec*>(hc);
+  MC_TRY(cudaStreamSynchronize(h->last_stream));
+  std::memset(out, 0, sizeof(*out));
+  out->n_kernels = kCgKernels;
+  for (int k = 0; k < kCgKernels; ++k) {
+    std::snprintf(out->name[k], sizeof(out->name[k]), "%s", kCgKernelNames[k]);
+    out->launches_timed[k] = h->prof_launches[k];
+    out->total_ms[k] = h->prof_ms[k];
+  }
+  return MC_OK;
 }
 
 mesh_codec_status_t mesh_codec_get_stats(const mesh_codec_t* hc, mesh_codec_stats_t* st) {

@@ -285,20 +285,30 @@ void cg_iteration(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_id
                   const int32_t* deg, const double* inv_d, const uint8_t* is_anchor,
                   const double* inv_diag, int kind, double* X, double* R, double* P, double* T,
                   double* Q, double rtol, int max_iters, CgState& st, cudaStream_t s,
-                  Launches& L) {
+                  Launches& L, cudaEvent_t* ev) {
   dim3 grid((g.W + 31) / 32, g.row_blocks);
   dim3 cgrid((g.W + 7) / 8);
+  if (ev) cudaEventRecord(ev[0], s);
   k_cg_L<<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, P, T, st.done);
+  if (ev) cudaEventRecord(ev[1], s);
   k_cg_LT<<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, is_anchor, T, P, Q,
                                        st.done, st.partials);
+  if (ev) cudaEventRecord(ev[2], s);
   k_cg_alpha<<<cgrid, 256, 0, s>>>(g, st.partials, st.rz, st.alpha, st.done, st.active);
+  if (ev) cudaEventRecord(ev[3], s);
   k_cg_update<<<grid, kCgThreads, 0, s>>>(g, X, R, P, Q, inv_diag, st.alpha, st.done,
                                            st.partials);
+  if (ev) cudaEventRecord(ev[4], s);
   k_cg_beta<<<cgrid, 256, 0, s>>>(g, st.partials, st.rz, st.rr, st.bb, st.beta, st.done,
                                   st.iters, rtol * rtol, max_iters, st.active);
+  if (ev) cudaEventRecord(ev[5], s);
   k_cg_dir<<<grid, kCgThreads, 0, s>>>(g, R, P, inv_diag, st.beta, st.done);
+  if (ev) cudaEventRecord(ev[6], s);
   L.add(6);
 }
+
+const char* const kCgKernelNames[kCgKernels] = {"k_cg_L", "k_cg_LT", "k_cg_alpha",
+                                                "k_cg_update", "k_cg_beta", "k_cg_dir"};
 
 // B[anchor a][coord_cols + f] += Ahat[a][f]   (P^T a^ for one coordinate block)
 __global__ void k_scatter_anchor_rhs(double* B, const double* __restrict__ Ahat,

@@ -159,7 +159,9 @@ void cg_iteration(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_id
                   const int32_t* deg, const double* inv_d, const uint8_t* is_anchor,
                   const double* inv_diag, int kind, double* X, double* R, double* P, double* T,
                   double* Q, double rtol, int max_iters, CgState& st, cudaStream_t s,
-                  Launches& L);
+                  Launches& L, cudaEvent_t* ev /* 7 events around the 6 kernels, or null */);
+constexpr int kCgKernels = 6;
+extern const char* const kCgKernelNames[kCgKernels];
 void scatter_anchor_rhs(double* B, const double* Ahat, const int32_t* anchors, int n_c, int F,
                         int W, int coord_cols, cudaStream_t s, Launches& L);
 void mark_anchors(const int32_t* anchors, int n_c, uint8_t* is_anchor, cudaStream_t s,
