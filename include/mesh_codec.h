@@ -222,6 +222,47 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_set_profiling(mesh_codec_t* h, int
 MESH_CODEC_API mesh_codec_status_t mesh_codec_get_profile(const mesh_codec_t* h,
                                                           mesh_codec_profile_t* out);
 
+/* Adjacency build that allocates nothing.  The paper has no counterpart:
+ * this is a service for callers that cannot call cudaMalloc where they
+ * need a mesh's adjacency, such as code running while its stream is being
+ * captured into a CUDA graph (allocation cannot be captured), real-time
+ * hosts that plan every allocation in advance, or plug-ins whose device
+ * memory belongs to another framework's allocator.
+ *
+ * Builds the same CSR adjacency as mesh_codec_create (MC_BUF_ROW_PTR,
+ * MC_BUF_COL_IDX, MC_BUF_DEGREE): every row sorted ascending, duplicates
+ * and the diagonal removed.
+ *   triangles:        device int32 [n_triangles][3], 0-based.
+ *   row_ptr:          device int32 [n_vertices + 1], written.
+ *   col_idx:          device int32 [col_idx_capacity]; nnz entries written.
+ *   deg:              device int32 [n_vertices], written.
+ *   nnz_out:          host; the number of adjacency entries (row_ptr[n]),
+ *                     also set on MC_E_BUFFER_TOO_SMALL.
+ * Limits: n_vertices <= MESH_CODEC_STATIC_MAX_VERTICES and n_triangles <=
+ * MESH_CODEC_STATIC_MAX_TRIANGLES; larger sizes return MC_E_INVALID_ARG
+ * before any work is enqueued.
+ * Memory: the call allocates no device or host memory (no cudaMalloc,
+ * cudaFree or allocating library call).  Its scratch is a static device
+ * array of 7,865,344 bytes (7.5 MiB) inside the library, which every GPU that loads the
+ * library holds until the process exits.  All calls share that array and it
+ * keeps the last call's contents; the call clears what must start at zero.
+ * Calls whose GPU work overlaps (other host threads, or streams not ordered
+ * with this one) race on it and must be serialised by the caller.
+ * The first call on each device looks up the array's device address with
+ * that device current; make that first call before any stream capture.
+ * Synchronises `stream` once (to read nnz and the error word); the
+ * compaction of col_idx is enqueued after that and is complete in stream
+ * order.  Errors: MC_E_INVALID_ARG, MC_E_BAD_MESH, MC_E_ISOLATED_VERTEX,
+ * MC_E_BUFFER_TOO_SMALL, MC_E_CUDA. */
+#define MESH_CODEC_STATIC_MAX_VERTICES (1 << 17)
+#define MESH_CODEC_STATIC_MAX_TRIANGLES (1 << 18)
+MESH_CODEC_API mesh_codec_status_t mesh_codec_adjacency_static(const int32_t* triangles,
+                                                               int n_triangles, int n_vertices,
+                                                               int32_t* row_ptr, int32_t* col_idx,
+                                                               size_t col_idx_capacity,
+                                                               int32_t* deg, int32_t* nnz_out,
+                                                               void* stream);
+
 /* Frees the handle and its workspace (synchronises the device first).
  * NULL is accepted. */
 MESH_CODEC_API void mesh_codec_destroy(mesh_codec_t* h);

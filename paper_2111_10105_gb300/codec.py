@@ -99,6 +99,9 @@ _SIGS = {
     "mesh_codec_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
     "mesh_codec_get_profile": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "mesh_codec_destroy": (None, [_P]),
+    "mesh_codec_adjacency_static": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P,
+                                                   ctypes.c_size_t, _P,
+                                                   ctypes.POINTER(ctypes.c_int32), _P]),
 }
 
 
