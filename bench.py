@@ -269,7 +269,8 @@ def run_ours(args):
     F, n = pos.shape[0], pos.shape[1]
     kw = dict(n_frames=F, rank=spec.rank, n_anchors=spec.n_anchors, seed=spec.seed,
               coeff_bits=spec.coeff_bits, dict_bits=spec.dict_bits,
-              anchor_bits=spec.anchor_bits, oi_sweeps=SWEEPS)
+              anchor_bits=spec.anchor_bits, oi_sweeps=SWEEPS,
+              solve_mode={"frames": 0, "factored": 1}[args.solve_mode])
     mc = MeshCodec(tris, n, **kw)
     pos_dev = torch.from_numpy(pos).to(dev)
     bits = torch.empty(mc.stream_bytes, dtype=torch.uint8, device=dev)
@@ -340,7 +341,8 @@ def run_ours(args):
 
     peaks = measured_peaks()
     nnz = int(mc.buffer(1).numel())
-    rl = roofline(profile, stats, n, 3 * F, nnz, spec.n_anchors, peaks)
+    cols = stats["cg_columns"]
+    rl = roofline(profile, stats, n, cols, nnz, spec.n_anchors, peaks)
 
     out = None
     if rank == 0:
@@ -353,7 +355,8 @@ def run_ours(args):
                        "k": spec.rank, "anchors": spec.n_anchors,
                        "bits": [spec.coeff_bits, spec.dict_bits, spec.anchor_bits],
                        "oi_sweeps": SWEEPS, "cg_rtol": 1e-14, "precision": "fp64",
-                       "decode_columns": 3 * F, "l2": "flushed (256 MiB write) before every step",
+                       "decode_columns": cols, "solve_mode": args.solve_mode,
+                       "l2": "flushed (256 MiB write) before every step",
                        "parallelism": f"replicas x{world}"},
             "nmse": nmse, "nmse_oracle": nmse_ref, "nmse_within_1e-9": bool(nmse_ok),
             "cg_iters_max": stats["cg_iters_max"], "cg_iters_mean": stats["cg_iters_mean"],
@@ -382,6 +385,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--solve-mode", choices=["frames", "factored"], default="frames",
+                    help="decoder right-hand sides: 3F frame columns (Eq. 11-12 as written) or "
+                         "3k + n_c factored columns (same solution, reassociated)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

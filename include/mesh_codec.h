@@ -64,8 +64,9 @@ typedef enum mesh_codec_precision {
 typedef enum mesh_codec_solve_mode {
     MC_SOLVE_FRAMES = 0,         /* one CG column per coordinate and frame (3F columns),
                                     the order of Eq. 11-12 */
-    MC_SOLVE_FACTORED = 1        /* 3k + n_c columns: M Y = L^T C'^T and M G = P^T, then
+    MC_SOLVE_FACTORED = 1,       /* 3k + n_c columns: M Y = L^T C'^T and M G = P^T, then
                                     X_c = Y_c U_c'^T + G a^_c (same solution, reassociated) */
+    MC_SOLVE_AUTO = 2            /* FACTORED when 3k + n_c < 3F, else FRAMES */
 } mesh_codec_solve_mode_t;
 
 typedef struct mesh_codec_params {
@@ -193,7 +194,8 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_get_stats(const mesh_codec_t* h, m
  *   MC_BUF_RITZ      float64 [3][k]   Ritz values (descending) of the last encode
  *   MC_BUF_COEFF     float64 [3][k][n] the projections C_c = U_c^T delta_c^T (Eq. 9)
  *   MC_BUF_START     float64 [3][F][k] the starting bases Q0_c
- *   MC_BUF_DELTA_REC float64 [n][3F]  decoded delta coordinates of the last decode
+ *   MC_BUF_DELTA_REC float64 [n][3F]  decoded delta coordinates of the last decode (FRAMES
+ *                                     mode; the FACTORED decode leaves X there instead)
  *   MC_BUF_CG_ITERS  int32 [columns]  CG iterations per column of the last decode */
 typedef enum mesh_codec_buffer {
     MC_BUF_ROW_PTR = 0, MC_BUF_COL_IDX = 1, MC_BUF_DEGREE = 2, MC_BUF_ANCHORS = 3,

@@ -23,6 +23,7 @@ STATUS_NAMES = {
 MC_PRECISION_FP64 = 0
 MC_SOLVE_FRAMES = 0
 MC_SOLVE_FACTORED = 1
+MC_SOLVE_AUTO = 2
 
 BUF_ROW_PTR, BUF_COL_IDX, BUF_DEGREE, BUF_ANCHORS = 0, 1, 2, 3
 BUF_DELTA, BUF_BASIS, BUF_RITZ, BUF_COEFF, BUF_START = 4, 5, 6, 7, 8

@@ -78,7 +78,8 @@ struct Carver {
 // lay out (or measure, when base == nullptr) the workspace
 size_t carve(mesh_codec* h, void* base) {
   Carver c(base);
-  const size_t n = h->n, F = h->F, k = h->k, W = h->W, nc = std::max(h->n_c, 1);
+  const size_t n = h->n, F = h->F, k = h->k, nc = std::max(h->n_c, 1);
+  const size_t W = std::max<size_t>(h->W, 3 * k + h->n_c);   // CG columns, either mode
   const size_t nnz_max = 6ull * h->T;
   h->row_ptr = c.take<int32_t>(n + 1);
   h->col_idx = c.take<int32_t>(nnz_max);
@@ -121,7 +122,8 @@ size_t carve(mesh_codec* h, void* base) {
   h->cg.beta = c.take<double>(W);
   h->cg.done = c.take<int32_t>(W);
   h->cg.iters = c.take<int32_t>(W);
-  h->cg.partials = c.take<double>(cg_partials_elems(h->n, h->W));
+  h->cg.partials = c.take<double>(std::max(cg_partials_elems(h->n, h->W),
+                                          cg_partials_elems(h->n, 3 * h->k + h->n_c)));
   h->cg.active = c.take<int32_t>(1);
   h->cg.all_done = c.take<int32_t>(1);
   h->d_status = c.take<uint32_t>(4);
@@ -177,7 +179,7 @@ bool valid_params(const mesh_codec_params_t* p) {
   if (p->precision != MC_PRECISION_FP64) return false;
   if (p->oi_sweeps < 0 || p->cg_max_iters < 1) return false;
   if (!(p->oi_tol >= 0.0) || !(p->cg_rtol >= 0.0)) return false;
-  if (p->solve_mode != MC_SOLVE_FRAMES) return false;
+  if (p->solve_mode < MC_SOLVE_FRAMES || p->solve_mode > MC_SOLVE_AUTO) return false;
   // 3F columns x n rows must be indexable, and the per-coordinate product fit
   if ((long long)p->n_frames * 3 > (1LL << 30)) return false;
   if ((long long)p->n_vertices * 3 * p->n_frames > (1LL << 40)) return false;
@@ -485,6 +487,13 @@ static void prof_collect(mesh_codec* h) {
   h->prof_used = 0;
 }
 
+// the factored decode solves 3k + n_c columns instead of 3F
+static bool use_factored(const mesh_codec* h) {
+  if (h->p.solve_mode == MC_SOLVE_FACTORED) return true;
+  if (h->p.solve_mode == MC_SOLVE_AUTO) return 3 * h->k + h->n_c < 3 * h->F;
+  return false;
+}
+
 static mesh_codec_status_t enqueue_decode(mesh_codec* h, const uint8_t* in, double* out,
                                           cudaStream_t s, Launches& L) {
   const int n = h->n, F = h->F, k = h->k, W = h->W;
@@ -496,23 +505,35 @@ static mesh_codec_status_t enqueue_decode(mesh_codec* h, const uint8_t* in, doub
   mark_anchors(h->dec_anchors, h->n_c, h->is_anchor, s, L);
   vertex_scalars_marked(h->row_ptr, h->col_idx, h->deg, h->is_anchor, n, h->kind, h->inv_d,
                         h->inv_diag, s, L);
-  // delta~_c = (U_c' C_c')^T : (n x k)(k x F) into D[:, cF : cF + F]
-  dgemm(n, F, k, 3, Strided{h->Cdeq, 1, n, (long long)k * n}, Strided{h->Udeq, 1, k, (long long)F * k},
-        StridedOut{h->D, W, 1, F}, 1, nullptr, s, L);
-  // B = L^T delta~ + P^T a^
-  laplacian_t_rows(h->row_ptr, h->col_idx, h->deg, h->inv_d, h->D, h->B, n, W, h->kind, s, L);
-  for (int c = 0; c < 3; ++c)
-    scatter_anchor_rhs(h->B, h->Ahat + (long long)c * std::max(h->n_c, 1) * F, h->dec_anchors,
-                       h->n_c, F, W, c * F, s, L);
+  const bool factored = use_factored(h);
+  // CG columns: 3F frames (Eq. 11-12 as written), or 3k + n_c factored columns
+  const int Wc = factored ? 3 * k + h->n_c : W;
+  const CgGeom geom = cg_geometry(n, Wc);
+  if (!factored) {
+    // delta~_c = (U_c' C_c')^T : (n x k)(k x F) into D[:, cF : cF + F]
+    dgemm(n, F, k, 3, Strided{h->Cdeq, 1, n, (long long)k * n},
+          Strided{h->Udeq, 1, k, (long long)F * k}, StridedOut{h->D, W, 1, F}, 1, nullptr, s, L);
+    // B = L^T delta~ + P^T a^
+    laplacian_t_rows(h->row_ptr, h->col_idx, h->deg, h->inv_d, h->D, h->B, n, W, h->kind, s, L);
+    for (int c = 0; c < 3; ++c)
+      scatter_anchor_rhs(h->B, h->Ahat + (long long)c * std::max(h->n_c, 1) * F, h->dec_anchors,
+                         h->n_c, F, W, c * F, s, L);
+  } else {
+    // E = [C_x'^T | C_y'^T | C_z'^T | 0] (n x Wc); B = L^T E, then column 3k + a of B
+    // gets e_{anchor a}:  M Y = L^T C'^T and M G = P^T
+    factored_rhs(h->Cdeq, k, n, Wc, h->D, s, L);
+    laplacian_t_rows(h->row_ptr, h->col_idx, h->deg, h->inv_d, h->D, h->B, n, Wc, h->kind, s, L);
+    unit_anchor_columns(h->B, h->dec_anchors, h->n_c, Wc, 3 * k, s, L);
+  }
   // CG
-  cg_init(h->geom, h->B, h->X, h->R, h->P, h->inv_diag, h->cg, s, L);
-  h->cg_columns = W;
+  cg_init(geom, h->B, h->X, h->R, h->P, h->inv_diag, h->cg, s, L);
+  h->cg_columns = Wc;
   const int batch = 32;
   int it = 0;
   while (it < h->p.cg_max_iters) {
     int m = std::min(batch, h->p.cg_max_iters - it);
     for (int j = 0; j < m; ++j)
-      cg_iteration(h->geom, h->row_ptr, h->col_idx, h->deg, h->inv_d, h->is_anchor, h->inv_diag,
+      cg_iteration(geom, h->row_ptr, h->col_idx, h->deg, h->inv_d, h->is_anchor, h->inv_diag,
                    h->kind, h->X, h->R, h->P, h->Tv, h->Qv, h->p.cg_rtol, h->p.cg_max_iters, h->cg,
                    s, L, prof_group(h, it + j));
     it += m;
@@ -520,7 +541,18 @@ static mesh_codec_status_t enqueue_decode(mesh_codec* h, const uint8_t* in, doub
     MC_TRY(cudaStreamSynchronize(s));
     if (*h->h_active == 0) break;
   }
-  vertex_major_to_frames(h->X, out, F, n, s, L);
+  if (!factored) {
+    vertex_major_to_frames(h->X, out, F, n, s, L);
+    return MC_OK;
+  }
+  // X_c = Y_c U_c'^T + G A^_c into D [n][3F]
+  dgemm(n, F, k, 3, Strided{h->X, Wc, 1, k}, Strided{h->Udeq, 1, k, (long long)F * k},
+        StridedOut{h->D, W, 1, F}, 1, nullptr, s, L);
+  StridedOut acc{h->D, W, 1, F};
+  acc.accumulate = 1;
+  dgemm(n, F, h->n_c, 3, Strided{h->X + 3 * k, Wc, 1, 0},
+        Strided{h->Ahat, F, 1, (long long)std::max(h->n_c, 1) * F}, acc, 1, nullptr, s, L);
+  vertex_major_to_frames(h->D, out, F, n, s, L);
   return MC_OK;
 }
 
@@ -545,7 +577,8 @@ mesh_codec_status_t mesh_codec_decode(mesh_codec_t* h, const uint8_t* bitstream,
   Launches L{&h->launches_decode};
   st = enqueue_decode(h, bitstream, positions_out, s, L);
   if (st != MC_OK) return st;
-  k_flag_not_converged<<<(h->W + 255) / 256, 256, 0, s>>>(h->cg.done, h->W, h->d_status);
+  k_flag_not_converged<<<(h->cg_columns + 255) / 256, 256, 0, s>>>(h->cg.done, h->cg_columns,
+                                                                     h->d_status);
   L.add(1);
   MC_TRY(cudaGetLastError());
   st = read_status(h, s);
@@ -596,7 +629,8 @@ mesh_codec_status_t mesh_codec_decode_host(mesh_codec_t* h, const uint8_t* bitst
   Launches L{&h->launches_decode};
   st = enqueue_decode(h, h->stage_bits, h->stage_pos, s, L);
   if (st != MC_OK) return st;
-  k_flag_not_converged<<<(h->W + 255) / 256, 256, 0, s>>>(h->cg.done, h->W, h->d_status);
+  k_flag_not_converged<<<(h->cg_columns + 255) / 256, 256, 0, s>>>(h->cg.done, h->cg_columns,
+                                                                     h->d_status);
   L.add(1);
   MC_TRY(cudaMemcpyAsync(positions_out_host, h->stage_pos, sizeof(double) * 3ull * h->n * h->F,
                          cudaMemcpyDeviceToHost, s));

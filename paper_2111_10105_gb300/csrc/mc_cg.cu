@@ -321,6 +321,45 @@ __global__ void k_scatter_anchor_rhs(double* B, const double* __restrict__ Ahat,
   }
 }
 
+// E[i][c*k + r] = C'_c[r][i] for c < 3, r < k; E[i][3k + a] = 0   (E: [n][Wc])
+__global__ void k_factored_rhs(const double* __restrict__ Cdeq, int k, int n, int Wc,
+                               double* __restrict__ E) {
+  const long long total = (long long)n * Wc;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long i = e / Wc;
+    int col = (int)(e % Wc);
+    double v = 0.0;
+    if (col < 3 * k) {
+      int c = col / k, r = col % k;
+      v = Cdeq[((long long)c * k + r) * n + i];
+    }
+    E[e] = v;
+  }
+}
+
+void factored_rhs(const double* Cdeq, int k, int n, int Wc, double* E, cudaStream_t s,
+                  Launches& L) {
+  long long total = (long long)n * Wc;
+  int grid = (int)std::min<long long>((total + 255) / 256, 152 * 32);
+  k_factored_rhs<<<grid, 256, 0, s>>>(Cdeq, k, n, Wc, E);
+  L.add(1);
+}
+
+// B[anchor a][col0 + a] += 1   (the columns of P^T)
+__global__ void k_unit_anchor_columns(double* B, const int32_t* __restrict__ anchors, int n_c,
+                                      int Wc, int col0) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n_c; a += gridDim.x * blockDim.x)
+    B[(long long)anchors[a] * Wc + col0 + a] += 1.0;
+}
+
+void unit_anchor_columns(double* B, const int32_t* anchors, int n_c, int Wc, int col0,
+                         cudaStream_t s, Launches& L) {
+  if (n_c <= 0) return;
+  k_unit_anchor_columns<<<(n_c + 255) / 256, 256, 0, s>>>(B, anchors, n_c, Wc, col0);
+  L.add(1);
+}
+
 void scatter_anchor_rhs(double* B, const double* Ahat, const int32_t* anchors, int n_c, int F,
                         int W, int coord_cols, cudaStream_t s, Launches& L) {
   if (n_c <= 0) return;

@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(NT) k_dgemm(int M, int N, int K, int batch, in
       int nc = n0 + tx * 4 + j;
       if (nc >= N) continue;
       if (splits == 1) {
-        C.p[(long long)b * C.sb + (long long)m * C.s0 + (long long)nc * C.s1] = acc[i][j];
+        double* cp = C.p + (long long)b * C.sb + (long long)m * C.s0 + (long long)nc * C.s1;
+        *cp = C.accumulate ? *cp + acc[i][j] : acc[i][j];
       } else {
         partials[(((long long)split * batch + b) * M + m) * N + nc] = acc[i][j];
       }
@@ -95,7 +96,8 @@ __global__ void k_reduce_partials(int M, int N, int batch, int splits,
     for (int z = 0; z < splits; ++z) s += partials[(long long)z * total + e];
     long long b = e / ((long long)M * N), r = e % ((long long)M * N);
     long long m = r / N, nc = r % N;
-    C.p[b * C.sb + m * C.s0 + nc * C.s1] = s;
+    double* cp = C.p + b * C.sb + m * C.s0 + nc * C.s1;
+    *cp = C.accumulate ? *cp + s : s;
   }
 }
 

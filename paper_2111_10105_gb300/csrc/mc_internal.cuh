@@ -91,6 +91,7 @@ struct Strided {  // element (r, c) at p[r*s0 + c*s1] + batch*sb
 struct StridedOut {
   double* p;
   long long s0, s1, sb;
+  int accumulate = 0;   // 1: C += A B
 };
 // C(b) = A(b) B(b) for b < batch, (M x K)(K x N); split-K into `splits` partial
 // sums reduced in fixed order (partials: splits*batch*M*N doubles)
@@ -164,6 +165,10 @@ constexpr int kCgKernels = 6;
 extern const char* const kCgKernelNames[kCgKernels];
 void scatter_anchor_rhs(double* B, const double* Ahat, const int32_t* anchors, int n_c, int F,
                         int W, int coord_cols, cudaStream_t s, Launches& L);
+void factored_rhs(const double* Cdeq, int k, int n, int Wc, double* E, cudaStream_t s,
+                  Launches& L);
+void unit_anchor_columns(double* B, const int32_t* anchors, int n_c, int Wc, int col0,
+                         cudaStream_t s, Launches& L);
 void mark_anchors(const int32_t* anchors, int n_c, uint8_t* is_anchor, cudaStream_t s,
                   Launches& L);
 

@@ -240,14 +240,16 @@ def test_full_rank_raw_roundtrip():
 
 
 # ------------------------------------------------------------------ decoder
-@pytest.mark.parametrize("level,F,k,n_c", [(3, 37, 5, 11), (4, 64, 16, 20)])
-def test_decoder_nmse_parity(level, F, k, n_c):
+@pytest.mark.parametrize("level,F,k,n_c,mode", [(3, 37, 5, 11, 0), (4, 64, 16, 20, 0),
+                                                (3, 37, 5, 11, 1), (4, 64, 16, 20, 1),
+                                                (4, 64, 16, 20, 2)])
+def test_decoder_nmse_parity(level, F, k, n_c, mode):
     spec, tris, pos = _seq(level=level, F=F, k=k, n_c=n_c, seed=2000 + level)
     p = _oracle_params(spec, oi_sweeps=30)
     o = oc.encode(tris, pos, p)
     rec_o = oc.decode(o, tris)
     n = pos.shape[1]
-    with _codec(tris, n, **_gpu_kw(p)) as mc:
+    with _codec(tris, n, solve_mode=mode, **_gpu_kw(p)) as mc:
         # decode the oracle's own stream: isolates the decoder
         ot = torch.from_numpy(np.frombuffer(o, dtype=np.uint8).copy()).cuda()
         rec_g = mc.decode(ot).cpu().numpy()
@@ -317,7 +319,8 @@ def test_cg_cap_reports_not_converged():
 
 # ------------------------------------------------------------------ full size
 @pytest.mark.slow
-def test_mid_config_parity_full_size():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_mid_config_parity_full_size(mode):
     """The 20 000-vertex torus sequence (F = 256, k = 32, 50 anchors) in the
     configuration the benchmark times."""
     spec = config_spec("torus200x100_F256_k32")
@@ -325,7 +328,7 @@ def test_mid_config_parity_full_size():
     p = _oracle_params(spec, oi_sweeps=30)
     o, info = oc.encode(tris, pos, p, return_info=True)
     n = pos.shape[1]
-    with _codec(tris, n, **_gpu_kw(p)) as mc:
+    with _codec(tris, n, solve_mode=mode, **_gpu_kw(p)) as mc:
         pt = torch.from_numpy(pos).cuda()
         g = mc.encode(pt)
         gb = bytes(g.cpu().numpy().tobytes())
