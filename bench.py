@@ -385,7 +385,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--solve-mode", choices=["frames", "factored"], default="frames",
+    ap.add_argument("--solve-mode", choices=["frames", "factored"], default="factored",
                     help="decoder right-hand sides: 3F frame columns (Eq. 11-12 as written) or "
                          "3k + n_c factored columns (same solution, reassociated)")
     args = ap.parse_args(argv)
