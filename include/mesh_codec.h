@@ -224,6 +224,17 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_set_profiling(mesh_codec_t* h, int
 MESH_CODEC_API mesh_codec_status_t mesh_codec_get_profile(const mesh_codec_t* h,
                                                           mesh_codec_profile_t* out);
 
+/* Test entry point for the tensor-core GEMM behind the mixed-precision modes:
+ * C (M x N, float64) = A (M x K) * B^T with A, B float32 device row-major
+ * [M][K] and [N][K], operands rounded to TF32 (kind 0) or BF16 (kind 1),
+ * products accumulated in FP32 on tcgen05 tensor cores per K split, splits
+ * summed in FP64.  Allocates and frees its own temporaries; synchronises
+ * `stream`.  Errors: MC_E_INVALID_ARG, MC_E_OOM, MC_E_CUDA. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_selftest_gemm(int kind, int M, int N, int K,
+                                                            int splits, const float* A,
+                                                            const float* B, double* C,
+                                                            void* stream);
+
 /* Adjacency build that allocates nothing.  The paper has no counterpart:
  * this is a service for callers that cannot call cudaMalloc where they
  * need a mesh's adjacency, such as code running while its stream is being

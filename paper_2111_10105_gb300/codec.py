@@ -100,6 +100,8 @@ _SIGS = {
     "mesh_codec_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
     "mesh_codec_get_profile": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "mesh_codec_destroy": (None, [_P]),
+    "mesh_codec_selftest_gemm": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
     "mesh_codec_adjacency_static": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P,
                                                    ctypes.c_size_t, _P,
                                                    ctypes.POINTER(ctypes.c_int32), _P]),
@@ -308,3 +310,22 @@ def _host_ptr(obj, dtype, shape):
         a = np.frombuffer(obj, dtype=np.uint8)
         return ctypes.c_void_p(a.ctypes.data), a
     raise TypeError("unsupported host buffer")
+
+
+def selftest_gemm(kind, A, B, splits=1, stream=None):
+    """C = A B^T on the tensor cores (kind 0: TF32, 1: BF16 operands, FP32
+    accumulation per K split, FP64 sum of splits).  A, B: CUDA float32
+    [M, K] and [N, K]."""
+    torch = _torch()
+    lib = load_library()
+    A = A.contiguous()
+    B = B.contiguous()
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty((M, N), dtype=torch.float64, device=A.device)
+    _check(lib.mesh_codec_selftest_gemm(int(kind), M, N, K, int(splits),
+                                        ctypes.c_void_p(A.data_ptr()),
+                                        ctypes.c_void_p(B.data_ptr()),
+                                        ctypes.c_void_p(C.data_ptr()), _stream_ptr(stream)),
+           "mesh_codec_selftest_gemm")
+    return C

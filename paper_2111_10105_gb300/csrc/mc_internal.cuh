@@ -27,6 +27,7 @@ enum : uint32_t {
   ST_BAD_ANCHORS = 1u << 4,
   ST_NOT_CONVERGED = 1u << 5,
   ST_BITSTREAM = 1u << 6,
+  ST_TC_TIMEOUT = 1u << 7,   // a tensor-core GEMM wait ran out (bounded mbarrier wait)
 };
 
 // splitmix64 (Steele, Lea, Flood 2014): output i of the generator seeded with s.
@@ -108,6 +109,26 @@ void oi_change(const double* Qold, const double* Qnew, int F, int k, double* wor
 void jacobi_eig(const double* H, double* V, double* theta, int k, cudaStream_t s,
                 Launches& L);
 void sign_rule(double* U, int F, int k, cudaStream_t s, Launches& L);
+
+// ---------------------------------------------------------------- tensor cores
+// TMA descriptor (CUtensorMap, 128 bytes, 64-byte aligned storage at map_out)
+// of a rows x K operand, K innermost, for tcgen05 tiles (128-byte swizzle).
+bool tc_operand_map(void* map_out, const void* base, int elem_bytes, long long K, long long rows,
+                    int batch, long long pitch, long long bpitch, int box_rows);
+inline int tc_bn(int N) { return N <= 256 ? ((N + 15) / 16) * 16 : 256; }
+size_t tc_smem_bytes(int BN);
+// D = A B^T (FP32 accumulate) on tcgen05; kind 0 tf32, 1 bf16; returns splits used
+int umma_tn(int kind, const void* mapA, const void* mapB, int M, int N, int K, int batch,
+            int splits, float* out, long long s0, long long s1, long long sb,
+            long long split_stride, uint32_t* status, cudaStream_t s, Launches& L);
+void pack_operand_f64(const double* src, long long ssb, long long sr, long long sc, int batch,
+                      long long rows, long long cols, long long dcols, long long dpitch,
+                      long long dbp, int kind, void* dst, cudaStream_t s, Launches& L);
+void pack_operand_f32(const float* src, long long ssb, long long sr, long long sc, int batch,
+                      long long rows, long long cols, long long dcols, long long dpitch,
+                      long long dbp, int kind, void* dst, cudaStream_t s, Launches& L);
+void sum_splits(const float* part, int splits, long long stride, long long count, double* out,
+                cudaStream_t s, Launches& L);
 
 // ---------------------------------------------------------------- quantizer
 struct Section {     // one coded section of the bitstream
