@@ -4,15 +4,19 @@
 One step = one encode (delta coordinates, orthogonal iterations, projection,
 quantization and packing) plus one decode (unpacking, back-projection,
 right-hand sides, anchored least-squares CG solve, output) of one synthetic
-sequence, with the input already resident in device memory.  The workload is
-the 20 000-vertex torus sequence (F = 256 frames, k = 32, 12-bit
-coefficients, 16-bit dictionary and anchors, 50 anchors) in the FP64 mode.
+sequence, with the input already resident in device memory.  The default
+workload is the 20 000-vertex torus sequence (F = 256 frames, k = 32,
+12-bit coefficients, 16-bit dictionary and anchors, 50 anchors) in the FP64
+mode; `--workload grid316_F512_k64 --precision tf32` measures the
+mixed-precision form on the 99 856-vertex grid sequence.
 
 Prints ONE JSON line (rank 0).  Under torchrun each rank runs an independent
 replica on its own GPU (the codec does not shard a sequence); `value` is the
 vertex-frames of all ranks divided by the slowest rank's time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME] [--precision fp64|tf32|bf16]
+                    [--solve-mode factored|frames]
 """
 
 import argparse
@@ -22,7 +26,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -31,12 +34,13 @@ if ROOT not in sys.path:
 
 METRIC = "encode+decode vertex-frames/s at fixed NMSE vs FP64 oracle; % of HBM/TC roofline"
 UNIT = "vertex-frames/s"
-WORKLOAD = "torus200x100_F256_k32"
+DEFAULT_WORKLOAD = "torus200x100_F256_k32"
 SWEEPS = 30
-NMSE_RTOL = 1e-9
+# stated NMSE bounds relative to the FP64 oracle's NMSE, per precision mode
+NMSE_RTOL = {"fp64": 1e-9, "tf32": 1e-2, "bf16": 1e-1}
+PRECISION_CODE = {"fp64": 0, "tf32": 1, "bf16": 2}
 # FP64 peak of a GB300: 152 SMs x 2 FP64 FMA per SM per clock x 2 flop x 2.07 GHz
-# (the nominal 1.25 TFLOP/s divided by the SM count and the maximum SM clock
-# gives 3.97 flop per SM per clock).
+# (ncu reports 304 DFMA thread instructions per cycle for the whole GPU).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 CPU_SAMPLE_FRAMES = 64       # cpu_baseline: first 64 frames of the same sequence
@@ -54,13 +58,14 @@ def measured_peaks():
 
 
 def nmse_reference(workload):
+    """(sweeps, NMSE) stored by tests/golden/make_nmse_reference.py, or None."""
     path = os.path.join(ROOT, "tests", "golden", "nmse_reference.txt")
     with open(path) as f:
         for line in f:
             parts = line.split()
             if parts and not line.startswith("#") and parts[0] == workload:
                 return int(parts[1]), float(parts[2])
-    raise KeyError(workload)
+    return None
 
 
 def dist_env():
@@ -82,6 +87,29 @@ def aggregate(vf_local, seconds_local, world, dist=None):
         dist.all_reduce(v, op=dist.ReduceOp.SUM)
         return v.item() / t.item(), t.item()
     return vf_local / seconds_local, seconds_local
+
+
+def parse_clock_rows(text):
+    """Median SM clock, max clock and the throttle reasons seen, from
+    nvidia-smi CSV rows (index, sm, max sm, power, active, hw_slowdown,
+    hw_thermal, sw_thermal, sw_power_cap)."""
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in text.splitlines():
+        r = [x.strip() for x in line.split(",")]
+        if len(r) < 9:
+            continue
+        try:
+            sm.append(float(r[1]))
+            mx.append(float(r[2]))
+        except ValueError:
+            continue
+        for name, v in zip(names, r[5:9]):
+            if v.lower() == "active":
+                reasons.add(name)
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(mx) if mx else None,
+            "reasons": sorted(reasons), "samples": len(sm)}
 
 
 class ClockSampler:
@@ -118,45 +146,32 @@ class ClockSampler:
             self.proc.kill()
         self.file.flush()
         self.file.seek(0)
-        rows = [l.strip().split(", ") for l in self.file.read().splitlines() if l.strip()]
+        text = self.file.read()
         os.unlink(self.file.name)
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            if len(r) < 9:
-                continue
-            try:
-                sm.append(float(r[1]))
-                mx.append(float(r[2]))
-            except ValueError:
-                continue
-            for name, v in zip(names, r[5:9]):
-                if v.strip().lower() == "active":
-                    reasons.add(name)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return parse_clock_rows(text)
 
 
-def kernel_work(name, n, W_active, nnz, n_c):
-    """Algorithmic FP64 flops and bytes of one launch of a decoder CG kernel
-    (FMA = 2 flop), for W_active active columns over n vertices."""
+def kernel_work(name, n, W_active, nnz, n_c, eb=8):
+    """Algorithmic flops (FMA = 2) and bytes of one launch of a decoder CG
+    kernel, for W_active active columns over n vertices and eb-byte vector
+    elements (8: FP64 mode, 4: FP32 vectors of the mixed modes)."""
     e = n * W_active                      # vertex-column entries
     dbar = nnz / n
     csr = 4 * (n + 1) + 4 * nnz
     if name == "k_cg_L":
-        return e * (dbar + 2), e * 16 + csr + 8 * n
+        return e * (dbar + 2), e * 2 * eb + csr + 8 * n
     if name == "k_cg_LT":
-        return e * (2 * dbar + 3) + n_c * W_active, e * 24 + csr + 9 * n
+        return e * (2 * dbar + 3) + n_c * W_active, e * 3 * eb + csr + 9 * n
     if name == "k_cg_update":
-        return e * 9, e * 48 + 8 * n
+        return e * 9, e * 6 * eb + 8 * n
     if name == "k_cg_dir":
-        return e * 3, e * 24 + 8 * n
+        return e * 3, e * 3 * eb + 8 * n
     return 0.0, 0.0
 
 
-def roofline(profile, stats, n, W, nnz, n_c, peaks):
-    """Dominant CG kernel's achieved FP64 rate against the FP64 peak."""
+def roofline(profile, stats, n, W, nnz, n_c, peaks, single):
+    """Dominant CG kernel against its roofline: the FP64 pipe in the FP64
+    mode, HBM bandwidth for the FP32 vectors of the mixed modes."""
     best, best_ms = None, -1.0
     shares = {}
     total = sum(ms for (_, ms) in profile.values())
@@ -168,22 +183,30 @@ def roofline(profile, stats, n, W, nnz, n_c, peaks):
     launches, ms = profile[best]
     mean_s = ms / launches / 1e3
     W_active = W * stats["cg_iters_mean"] / max(1, stats["cg_iters_max"])
-    flops, nbytes = kernel_work(best, n, W_active, nnz, n_c)
-    achieved = flops / mean_s / 1e12
-    return {
-        "kernel": best, "bound": "alu", "achieved": round(achieved, 4),
-        "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-        "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
-        "algorithmic_bytes": int(nbytes), "mean_launch_ms": round(mean_s * 1e3, 5),
-        "hbm_GBps_at_algorithmic_bytes": round(nbytes / mean_s / 1e9, 1),
-        "hbm_peak_GBps": peaks.get("hbm_gbs"),
-        "launches_timed": launches, "time_share": {k: round(v, 4) for k, v in shares.items()},
-        "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-    }
+    flops, nbytes = kernel_work(best, n, W_active, nnz, n_c, 4 if single else 8)
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    out = {"kernel": best, "traffic": None, "algorithmic_bytes": int(nbytes),
+           "algorithmic_flops": int(flops), "mean_launch_ms": round(mean_s * 1e3, 5),
+           "launches_timed": launches,
+           "time_share": {k: round(v, 4) for k, v in shares.items()}}
+    if single:
+        achieved = nbytes / mean_s / 1e9
+        out.update({"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(achieved / hbm, 4),
+                    "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"
+                    if peaks.get("hbm_gbs") else "fallback 6.8 TB/s"})
+    else:
+        achieved = flops / mean_s / 1e12
+        out.update({"bound": "alu", "achieved": round(achieved, 4),
+                    "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                    "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                    "hbm_GBps_at_algorithmic_bytes": round(nbytes / mean_s / 1e9, 1)})
+    return out
 
 
 # ---------------------------------------------------------------- oracle legs
-def oracle_sample(frames, repeats=1):
+def oracle_sample(workload, frames, repeats=1):
     """Time the FP64 oracle (single-threaded BLAS) on the first `frames`
     frames of the workload's sequence, in a child process."""
     env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1",
@@ -202,19 +225,19 @@ def oracle_sample(frames, repeats=1):
         "    out.append([t1 - t0, t2 - t1])\n"
         "print(json.dumps({'n': pos.shape[1], 'F': pos.shape[0], 'times': out,"
         " 'nmse': metrics.nmse(pos, rec)}))\n"
-    ) % (ROOT, WORKLOAD, frames, SWEEPS, repeats)
+    ) % (ROOT, workload, frames, SWEEPS, repeats)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline():
-    res = oracle_sample(CPU_SAMPLE_FRAMES, repeats=1)
+def cpu_baseline(workload):
+    res = oracle_sample(workload, CPU_SAMPLE_FRAMES, repeats=1)
     enc, dec = res["times"][0]
     vf = res["n"] * res["F"]
     return {"value": vf / (enc + dec), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"{WORKLOAD} first {res['F']} frames (n={res['n']}), one encode+decode, "
+            "sample": (f"{workload} first {res['F']} frames (n={res['n']}), one encode+decode, "
                        f"single-threaded numpy/scipy, encode {enc:.2f} s + decode {dec:.2f} s")}
 
 
@@ -223,9 +246,9 @@ def run_reference(args):
     if rank != 0:
         return 0
     for _ in range(args.warmup):
-        oracle_sample(REF_SAMPLE_FRAMES, repeats=1)
+        oracle_sample(args.workload, REF_SAMPLE_FRAMES, repeats=1)
     t0 = time.perf_counter()
-    res = oracle_sample(REF_SAMPLE_FRAMES, repeats=args.steps)
+    res = oracle_sample(args.workload, REF_SAMPLE_FRAMES, repeats=args.steps)
     wall = time.perf_counter() - t0
     secs = sum(a + b for a, b in res["times"])
     vf = res["n"] * res["F"] * args.steps
@@ -235,10 +258,10 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD} (first {res['F']} frames per step)",
+        "config": {"workload": f"{args.workload} (first {res['F']} frames per step)",
                    "n": res["n"], "F": res["F"], "sweeps": SWEEPS},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{WORKLOAD} first {res['F']} frames, single-threaded, "
+                         "sample": f"{args.workload} first {res['F']} frames, single-threaded, "
                                    f"{args.steps} encode+decode passes ({wall:.1f} s wall)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "nmse": res["nmse"],
@@ -249,7 +272,6 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
-    import numpy as np
     import torch
 
     from oracle import metrics   # NMSE of the result, computed on the host
@@ -264,12 +286,16 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    spec = config_spec(WORKLOAD)
+    spec = config_spec(args.workload)
     tris, pos = make_sequence(spec)
     F, n = pos.shape[0], pos.shape[1]
+    prec = PRECISION_CODE[args.precision]
+    single = prec != 0
+    cg_rtol = 1e-6 if single else 1e-14
     kw = dict(n_frames=F, rank=spec.rank, n_anchors=spec.n_anchors, seed=spec.seed,
               coeff_bits=spec.coeff_bits, dict_bits=spec.dict_bits,
-              anchor_bits=spec.anchor_bits, oi_sweeps=SWEEPS,
+              anchor_bits=spec.anchor_bits, oi_sweeps=SWEEPS, precision=prec,
+              oi_refine_sweeps=1 if single else 0, cg_rtol=cg_rtol,
               solve_mode={"frames": 0, "factored": 1}[args.solve_mode])
     mc = MeshCodec(tris, n, **kw)
     pos_dev = torch.from_numpy(pos).to(dev)
@@ -284,7 +310,6 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         step()
-    stats = mc.stats()
     mc.set_profiling(16)
     uuid = None
     try:
@@ -320,9 +345,11 @@ def run_ours(args):
     value, seconds = aggregate(vf_local, total_ms / 1e3, world, dist)
 
     # NMSE of this run's reconstruction vs the oracle's stored value
-    sweeps_ref, nmse_ref = nmse_reference(WORKLOAD)
+    ref = nmse_reference(args.workload)
     nmse = metrics.nmse(pos, rec.cpu().numpy())
-    nmse_ok = sweeps_ref == SWEEPS and abs(nmse - nmse_ref) <= NMSE_RTOL * nmse_ref
+    tol = NMSE_RTOL[args.precision]
+    nmse_ref = ref[1] if ref and ref[0] == SWEEPS else None
+    nmse_ok = None if nmse_ref is None else abs(nmse - nmse_ref) <= tol * nmse_ref
 
     # end to end through the host-buffer entry points (pinned host memory)
     pos_h = torch.from_numpy(pos).pin_memory()
@@ -342,23 +369,27 @@ def run_ours(args):
     peaks = measured_peaks()
     nnz = int(mc.buffer(1).numel())
     cols = stats["cg_columns"]
-    rl = roofline(profile, stats, n, cols, nnz, spec.n_anchors, peaks)
+    rl = roofline(profile, stats, n, cols, nnz, spec.n_anchors, peaks, single)
 
-    out = None
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": seconds * 1e3 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "mesh": "closed torus grid 200x100", "n": n, "F": F,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "tf32": "tf32+f32 (FP64 QR, refinement, quantizer)",
+                      "bf16": "bf16+f32 (FP64 QR, refinement, quantizer)"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": args.workload, "mesh": spec.mesh, "n": n, "F": F,
                        "k": spec.rank, "anchors": spec.n_anchors,
                        "bits": [spec.coeff_bits, spec.dict_bits, spec.anchor_bits],
-                       "oi_sweeps": SWEEPS, "cg_rtol": 1e-14, "precision": "fp64",
+                       "oi_sweeps": SWEEPS, "oi_refine_sweeps": 1 if single else 0,
+                       "cg_rtol": cg_rtol, "precision": args.precision,
                        "decode_columns": cols, "solve_mode": args.solve_mode,
                        "l2": "flushed (256 MiB write) before every step",
                        "parallelism": f"replicas x{world}"},
-            "nmse": nmse, "nmse_oracle": nmse_ref, "nmse_within_1e-9": bool(nmse_ok),
+            "nmse": nmse, "nmse_oracle": nmse_ref, "nmse_rtol_bound": tol,
+            "nmse_within_bound": nmse_ok,
             "cg_iters_max": stats["cg_iters_max"], "cg_iters_mean": stats["cg_iters_mean"],
             "roofline": rl,
             "clocks": clocks,
@@ -369,7 +400,7 @@ def run_ours(args):
             "gpu_launches": launches,
         }
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline()
+            out["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(out), flush=True)
     mc.close()
     if dist is not None:
@@ -384,6 +415,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--precision", choices=["fp64", "tf32", "bf16"], default="fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solve-mode", choices=["frames", "factored"], default="factored",
                     help="decoder right-hand sides: 3F frame columns (Eq. 11-12 as written) or "

@@ -57,7 +57,13 @@ typedef enum mesh_codec_status {
 
 /* Precision of the encoder's dense products and of the decoder's solve. */
 typedef enum mesh_codec_precision {
-    MC_PRECISION_FP64 = 0        /* every step in binary64 */
+    MC_PRECISION_FP64 = 0,       /* every step in binary64 */
+    MC_PRECISION_TF32 = 1,       /* orthogonal-iteration sweeps, projection and
+                                    back-projection on tcgen05 tensor cores with TF32
+                                    operands and FP32 accumulation, then
+                                    oi_refine_sweeps FP64 sweeps and the FP64
+                                    Rayleigh-Ritz; QR, quantizer and solve stay FP64 */
+    MC_PRECISION_BF16 = 2        /* the same with BF16 operands */
 } mesh_codec_precision_t;
 
 /* How the decoder forms the right-hand sides of Eq. 12. */
@@ -86,7 +92,8 @@ typedef struct mesh_codec_params {
     double cg_rtol;              /* per-column stop: ||r|| <= cg_rtol * ||b|| */
     uint64_t seed;               /* anchors and the starting basis (splitmix64) */
     int32_t solve_mode;          /* mesh_codec_solve_mode_t */
-    int32_t reserved[7];         /* must be zero */
+    int32_t oi_refine_sweeps;    /* mixed precision: FP64 sweeps after the tensor-core ones */
+    int32_t reserved[6];         /* must be zero */
 } mesh_codec_params_t;
 
 typedef struct mesh_codec_stats {

@@ -21,6 +21,8 @@ STATUS_NAMES = {
     8: "MC_E_BUFFER_TOO_SMALL", 9: "MC_E_NUMERICAL", 10: "MC_E_BAD_ANCHORS",
 }
 MC_PRECISION_FP64 = 0
+MC_PRECISION_TF32 = 1
+MC_PRECISION_BF16 = 2
 MC_SOLVE_FRAMES = 0
 MC_SOLVE_FACTORED = 1
 MC_SOLVE_AUTO = 2
@@ -40,7 +42,7 @@ class Params(ctypes.Structure):
         ("oi_sweeps", ctypes.c_int32), ("cg_max_iters", ctypes.c_int32),
         ("oi_tol", ctypes.c_double), ("cg_rtol", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("solve_mode", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 7),
+        ("oi_refine_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6),
     ]
 
 

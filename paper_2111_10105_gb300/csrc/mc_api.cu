@@ -19,46 +19,7 @@
 
 using namespace mc;
 
-struct mesh_codec {
-  mesh_codec_params_t p;
-  int n, T, F, k, W, n_c, kind;
-  EncodeLayout lay;
-  CgGeom geom;
-  // device workspace (one allocation)
-  void* ws = nullptr;
-  size_t ws_bytes = 0;
-  int32_t *row_ptr, *col_idx, *deg, *anchors, *dec_anchors;
-  uint8_t* is_anchor;
-  double *inv_d, *inv_diag;
-  double *Q0, *Q, *Zb, *U, *V, *H, *theta, *Wk, *partials, *chg_work, *chg;
-  double *G, *Rf;
-  double *Cf, *qparams;
-  double *X, *D, *B, *R, *P, *Tv, *Qv;
-  double *Udeq, *Cdeq, *Ahat;
-  CgState cg;
-  uint32_t* d_status;
-  int nnz;
-  size_t partial_elems;
-  // host side
-  uint32_t* h_status = nullptr;     // pinned
-  int32_t* h_active = nullptr;      // pinned
-  uint8_t* h_header = nullptr;      // pinned, 64 bytes
-  double* h_chg = nullptr;          // pinned [3]
-  // staging for the host-buffer entry points (lazy)
-  double* stage_pos = nullptr;
-  uint8_t* stage_bits = nullptr;
-  cudaStream_t last_stream = nullptr;
-  uint64_t launches_create = 0, launches_encode = 0, launches_decode = 0;
-  int oi_done[3] = {0, 0, 0};
-  double oi_last_change[3] = {0, 0, 0};
-  int cg_columns = 0;
-  // kernel timing (mesh_codec_set_profiling)
-  int prof_every = 0;
-  std::vector<cudaEvent_t> prof_events;   // groups of kCgKernels + 1
-  size_t prof_used = 0;                    // groups recorded in the current decode
-  int64_t prof_launches[MESH_CODEC_PROF_KERNELS] = {0};
-  double prof_ms[MESH_CODEC_PROF_KERNELS] = {0};
-};
+#include "mc_handle.cuh"
 
 namespace {
 
@@ -127,7 +88,8 @@ size_t carve(mesh_codec* h, void* base) {
   h->cg.active = c.take<int32_t>(1);
   h->cg.all_done = c.take<int32_t>(1);
   h->d_status = c.take<uint32_t>(4);
-  return c.off + 256;
+  size_t off = mixed_carve(h, (char*)base, c.off);
+  return off + 1024;
 }
 
 int gemm_splits(long long K, long long tiles) {
@@ -176,14 +138,15 @@ bool valid_params(const mesh_codec_params_t* p) {
   if (p->anchor_bits < 0 || p->anchor_bits > MESH_CODEC_MAX_BITS) return false;
   if (p->n_anchors < 0 || p->n_anchors > p->n_vertices) return false;
   if (p->laplacian_kind != 0 && p->laplacian_kind != 1) return false;
-  if (p->precision != MC_PRECISION_FP64) return false;
+  if (p->precision < MC_PRECISION_FP64 || p->precision > MC_PRECISION_BF16) return false;
+  if (p->oi_refine_sweeps < 0) return false;
   if (p->oi_sweeps < 0 || p->cg_max_iters < 1) return false;
   if (!(p->oi_tol >= 0.0) || !(p->cg_rtol >= 0.0)) return false;
   if (p->solve_mode < MC_SOLVE_FRAMES || p->solve_mode > MC_SOLVE_AUTO) return false;
   // 3F columns x n rows must be indexable, and the per-coordinate product fit
   if ((long long)p->n_frames * 3 > (1LL << 30)) return false;
   if ((long long)p->n_vertices * 3 * p->n_frames > (1LL << 40)) return false;
-  for (int i = 0; i < 7; ++i)
+  for (int i = 0; i < 6; ++i)
     if (p->reserved[i] != 0) return false;
   return true;
 }
@@ -256,9 +219,11 @@ static mesh_codec_status_t create_impl(mesh_codec* h, const int32_t* tris_in, in
     size_t a = (size_t)sz * 3 * F * k, b = (size_t)sh * 3 * k * k, c = (size_t)sg * 3 * k * k;
     h->partial_elems = std::max(a, std::max(b, c));
   }
+  mixed_dims(h);
   h->ws_bytes = carve(h, nullptr);
   MC_TRY(cudaMalloc(&h->ws, h->ws_bytes));
   carve(h, h->ws);
+  if (!mixed_init(h, s)) return MC_E_CUDA;
   MC_TRY(cudaMallocHost(&h->h_status, sizeof(uint32_t) * 4));
   MC_TRY(cudaMallocHost(&h->h_active, sizeof(int32_t) * 4));
   MC_TRY(cudaMallocHost(&h->h_header, 64));
@@ -382,7 +347,13 @@ static void enqueue_encode(mesh_codec* h, const double* positions, uint8_t* out,
   const int sg = gemm_splits(F, ((k + 63) / 64) * ((k + 31) / 32));
   cudaMemcpyAsync(h->Q, h->Q0, sizeof(double) * 3 * F * k, cudaMemcpyDeviceToDevice, s);
   for (int c = 0; c < 3; ++c) { h->oi_done[c] = 0; h->oi_last_change[c] = 0.0; }
-  for (int t = 0; t < h->p.oi_sweeps; ++t) {
+  // mixed precision: tensor-core sweeps first, then the FP64 refinement sweeps
+  int fp64_sweeps = h->p.oi_sweeps;
+  if (h->lp >= 0) {
+    mixed_oi_sweeps(h, h->p.oi_sweeps, s, L);
+    fp64_sweeps = h->p.oi_refine_sweeps;
+  }
+  for (int t = 0; t < fp64_sweeps; ++t) {
     dgemm(n, k, F, 3, Xc, Strided{h->Q, k, 1, (long long)F * k},
           StridedOut{h->Wk, k, 1, (long long)n * k}, 1, nullptr, s, L);
     dgemm(F, k, n, 3, XcT, Strided{h->Wk, k, 1, (long long)n * k},
@@ -413,8 +384,12 @@ static void enqueue_encode(mesh_codec* h, const double* positions, uint8_t* out,
         StridedOut{h->U, k, 1, (long long)F * k}, 1, nullptr, s, L);
   sign_rule(h->U, F, k, s, L);
   // projection C_c = U_c^T delta_c^T (k x n)
-  dgemm(k, n, F, 3, Strided{h->U, 1, k, (long long)F * k}, Strided{h->D, 1, W, F},
-        StridedOut{h->Cf, n, 1, (long long)k * n}, 1, nullptr, s, L);
+  if (h->lp >= 0) {
+    mixed_project(h, s, L);
+  } else {
+    dgemm(k, n, F, 3, Strided{h->U, 1, k, (long long)F * k}, Strided{h->D, 1, W, F},
+          StridedOut{h->Cf, n, 1, (long long)k * n}, 1, nullptr, s, L);
+  }
   // quantizer ranges: dictionary columns, coefficient rows, anchors
   const long long P = 4LL * k + 2;
   minmax_rows_out(h->U, k, F, 1, k, 3, (long long)F * k, h->qparams, h->qparams + k, P, s, L);
@@ -511,8 +486,13 @@ static mesh_codec_status_t enqueue_decode(mesh_codec* h, const uint8_t* in, doub
   const CgGeom geom = cg_geometry(n, Wc);
   if (!factored) {
     // delta~_c = (U_c' C_c')^T : (n x k)(k x F) into D[:, cF : cF + F]
-    dgemm(n, F, k, 3, Strided{h->Cdeq, 1, n, (long long)k * n},
-          Strided{h->Udeq, 1, k, (long long)F * k}, StridedOut{h->D, W, 1, F}, 1, nullptr, s, L);
+    if (h->lp >= 0) {
+      mixed_backproject(h, s, L);
+    } else {
+      dgemm(n, F, k, 3, Strided{h->Cdeq, 1, n, (long long)k * n},
+            Strided{h->Udeq, 1, k, (long long)F * k}, StridedOut{h->D, W, 1, F}, 1, nullptr, s,
+            L);
+    }
     // B = L^T delta~ + P^T a^
     laplacian_t_rows(h->row_ptr, h->col_idx, h->deg, h->inv_d, h->D, h->B, n, W, h->kind, s, L);
     for (int c = 0; c < 3; ++c)
@@ -525,8 +505,9 @@ static mesh_codec_status_t enqueue_decode(mesh_codec* h, const uint8_t* in, doub
     laplacian_t_rows(h->row_ptr, h->col_idx, h->deg, h->inv_d, h->D, h->B, n, Wc, h->kind, s, L);
     unit_anchor_columns(h->B, h->dec_anchors, h->n_c, Wc, 3 * k, s, L);
   }
-  // CG
-  cg_init(geom, h->B, h->X, h->R, h->P, h->inv_diag, h->cg, s, L);
+  // CG: FP64 vectors, or FP32 vectors with FP64 dot products in the mixed modes
+  const int single = h->lp >= 0 ? 1 : 0;
+  cg_init(geom, h->B, h->X, h->R, h->P, h->inv_diag, h->cg, single, s, L);
   h->cg_columns = Wc;
   const int batch = 32;
   int it = 0;
@@ -535,22 +516,28 @@ static mesh_codec_status_t enqueue_decode(mesh_codec* h, const uint8_t* in, doub
     for (int j = 0; j < m; ++j)
       cg_iteration(geom, h->row_ptr, h->col_idx, h->deg, h->inv_d, h->is_anchor, h->inv_diag,
                    h->kind, h->X, h->R, h->P, h->Tv, h->Qv, h->p.cg_rtol, h->p.cg_max_iters, h->cg,
-                   s, L, prof_group(h, it + j));
+                   single, s, L, prof_group(h, it + j));
     it += m;
     MC_TRY(cudaMemcpyAsync(h->h_active, h->cg.active, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     MC_TRY(cudaStreamSynchronize(s));
     if (*h->h_active == 0) break;
   }
+  // the solution as FP64 (the mixed modes widen their FP32 iterate into B)
+  const double* Xs = h->X;
+  if (single) {
+    widen((const float*)h->X, (long long)n * Wc, h->B, s, L);
+    Xs = h->B;
+  }
   if (!factored) {
-    vertex_major_to_frames(h->X, out, F, n, s, L);
+    vertex_major_to_frames(Xs, out, F, n, s, L);
     return MC_OK;
   }
   // X_c = Y_c U_c'^T + G A^_c into D [n][3F]
-  dgemm(n, F, k, 3, Strided{h->X, Wc, 1, k}, Strided{h->Udeq, 1, k, (long long)F * k},
+  dgemm(n, F, k, 3, Strided{Xs, Wc, 1, k}, Strided{h->Udeq, 1, k, (long long)F * k},
         StridedOut{h->D, W, 1, F}, 1, nullptr, s, L);
   StridedOut acc{h->D, W, 1, F};
   acc.accumulate = 1;
-  dgemm(n, F, h->n_c, 3, Strided{h->X + 3 * k, Wc, 1, 0},
+  dgemm(n, F, h->n_c, 3, Strided{Xs + 3 * k, Wc, 1, 0},
         Strided{h->Ahat, F, 1, (long long)std::max(h->n_c, 1) * F}, acc, 1, nullptr, s, L);
   vertex_major_to_frames(h->D, out, F, n, s, L);
   return MC_OK;

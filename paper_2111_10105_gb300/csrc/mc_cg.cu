@@ -60,10 +60,39 @@ __device__ __forceinline__ void cta_col_partial(double v, double* sh, double* ou
   __syncthreads();
 }
 
+// Vector kernels, templated on the vector type T: double (FP64 mode) or
+// float (mixed modes: FP32 vectors and operator).  Dot products of FP32
+// vectors are accumulated per thread by Dot2 (Ogita, Rump, Oishi, "Accurate
+// sum and dot product", SIAM J. Sci. Comput. 2005: TwoProduct by FMA and
+// TwoSum, all on the FP32 pipe), which is as accurate as accumulating in
+// twice the working precision, and the per-thread results are combined in
+// FP64.
+template <typename T>
+struct DotAcc;
+template <>
+struct DotAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);            // a*b = p + e exactly
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));  // s+p = t+err
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(err, e));
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+template <typename T>
 __global__ void __launch_bounds__(kCgThreads) k_cg_init(CgGeom g, const double* __restrict__ B,
-                                                        double* __restrict__ X,
-                                                        double* __restrict__ R,
-                                                        double* __restrict__ P,
+                                                        T* __restrict__ X, T* __restrict__ R,
+                                                        T* __restrict__ P,
                                                         const double* __restrict__ inv_diag,
                                                         double* __restrict__ partials) {
   __shared__ double sh[256];
@@ -72,22 +101,22 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_init(CgGeom g, const double* 
   const bool valid = col < g.W;
   const long long r0 = (long long)blockIdx.y * g.rows_per_block;
   const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
-  double rz = 0.0, bb = 0.0;
+  DotAcc<T> rz, bb;
   if (valid) {
     for (long long i = r0 + rl; i < r1; i += 8) {
       long long e = i * g.W + col;
-      double b = B[e];
-      double z = b * inv_diag[i];
-      X[e] = 0.0;
+      const T b = (T)B[e];
+      const T z = b * (T)inv_diag[i];
+      X[e] = (T)0;
       R[e] = b;
       P[e] = z;
-      rz = fma(b, z, rz);
-      bb = fma(b, b, bb);
+      rz.add(b, z);
+      bb.add(b, b);
     }
   }
   const long long plane = (long long)g.row_blocks * g.W;
-  cta_col_partial(rz, sh, partials, col, g.W, valid);
-  cta_col_partial(bb, sh, partials + plane, col, g.W, valid);
+  cta_col_partial(rz.value(), sh, partials, col, g.W, valid);
+  cta_col_partial(bb.value(), sh, partials + plane, col, g.W, valid);
 }
 
 // one warp per column: fixed-order sum of the row-block partials
@@ -117,12 +146,12 @@ __global__ void k_cg_init_cols(CgGeom g, const double* __restrict__ partials, do
 }
 
 // T = L P for active columns
+template <typename T>
 __global__ void __launch_bounds__(kCgThreads) k_cg_L(CgGeom g, const int32_t* __restrict__ row_ptr,
                                                      const int32_t* __restrict__ col_idx,
                                                      const int32_t* __restrict__ deg,
                                                      const double* __restrict__ inv_d, int kind,
-                                                     const double* __restrict__ P,
-                                                     double* __restrict__ T,
+                                                     const T* __restrict__ P, T* __restrict__ Tv,
                                                      const int32_t* __restrict__ done) {
   const int col = blockIdx.x * 32 + (threadIdx.x & 31);
   const int rl = threadIdx.x >> 5;
@@ -131,22 +160,22 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_L(CgGeom g, const int32_t* __
   const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
   for (long long i = r0 + rl; i < r1; i += 8) {
     int b = row_ptr[i], e = row_ptr[i + 1];
-    double acc = 0.0;
+    T acc = (T)0;
     for (int p = b; p < e; ++p) acc += P[(long long)col_idx[p] * g.W + col];
-    double pi = P[i * g.W + col];
-    T[i * g.W + col] = (kind == 0) ? fma(-inv_d[i], acc, pi) : fma((double)deg[i], pi, -acc);
+    T pi = P[i * g.W + col];
+    Tv[i * g.W + col] = (kind == 0) ? fma(-(T)inv_d[i], acc, pi) : fma((T)deg[i], pi, -acc);
   }
 }
 
 // Q = L^T T + [anchor] P and partial pAp
+template <typename T>
 __global__ void __launch_bounds__(kCgThreads) k_cg_LT(CgGeom g, const int32_t* __restrict__ row_ptr,
                                                       const int32_t* __restrict__ col_idx,
                                                       const int32_t* __restrict__ deg,
                                                       const double* __restrict__ inv_d, int kind,
                                                       const uint8_t* __restrict__ is_anchor,
-                                                      const double* __restrict__ T,
-                                                      const double* __restrict__ P,
-                                                      double* __restrict__ Q,
+                                                      const T* __restrict__ Tv,
+                                                      const T* __restrict__ P, T* __restrict__ Q,
                                                       const int32_t* __restrict__ done,
                                                       double* __restrict__ partials) {
   __shared__ double sh[256];
@@ -155,28 +184,28 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_LT(CgGeom g, const int32_t* _
   const bool valid = col < g.W && !done[col];
   const long long r0 = (long long)blockIdx.y * g.rows_per_block;
   const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
-  double pap = 0.0;
+  DotAcc<T> pap;
   if (valid) {
     for (long long j = r0 + rl; j < r1; j += 8) {
       int b = row_ptr[j], e = row_ptr[j + 1];
-      double acc = 0.0;
+      T acc = (T)0;
       if (kind == 0) {
         for (int p = b; p < e; ++p) {
           int i = col_idx[p];
-          acc = fma(inv_d[i], T[(long long)i * g.W + col], acc);
+          acc = fma((T)inv_d[i], Tv[(long long)i * g.W + col], acc);
         }
       } else {
-        for (int p = b; p < e; ++p) acc += T[(long long)col_idx[p] * g.W + col];
+        for (int p = b; p < e; ++p) acc += Tv[(long long)col_idx[p] * g.W + col];
       }
-      double tj = T[j * g.W + col];
-      double q = (kind == 0) ? tj - acc : fma((double)deg[j], tj, -acc);
-      double pj = P[j * g.W + col];
+      T tj = Tv[j * g.W + col];
+      T q = (kind == 0) ? tj - acc : fma((T)deg[j], tj, -acc);
+      T pj = P[j * g.W + col];
       if (is_anchor[j]) q += pj;
       Q[j * g.W + col] = q;
-      pap = fma(pj, q, pap);
+      pap.add(pj, q);
     }
   }
-  cta_col_partial(pap, sh, partials, col, g.W, col < g.W);
+  cta_col_partial(pap.value(), sh, partials, col, g.W, col < g.W);
 }
 
 __global__ void k_cg_alpha(CgGeom g, const double* __restrict__ partials,
@@ -193,10 +222,11 @@ __global__ void k_cg_alpha(CgGeom g, const double* __restrict__ partials,
   }
 }
 
-__global__ void __launch_bounds__(kCgThreads) k_cg_update(CgGeom g, double* __restrict__ X,
-                                                          double* __restrict__ R,
-                                                          const double* __restrict__ P,
-                                                          const double* __restrict__ Q,
+template <typename T>
+__global__ void __launch_bounds__(kCgThreads) k_cg_update(CgGeom g, T* __restrict__ X,
+                                                          T* __restrict__ R,
+                                                          const T* __restrict__ P,
+                                                          const T* __restrict__ Q,
                                                           const double* __restrict__ inv_diag,
                                                           const double* __restrict__ alpha,
                                                           const int32_t* __restrict__ done,
@@ -207,22 +237,22 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_update(CgGeom g, double* __re
   const bool valid = col < g.W && !done[col];
   const long long r0 = (long long)blockIdx.y * g.rows_per_block;
   const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
-  double rz = 0.0, rr = 0.0;
+  DotAcc<T> rz, rr;
   if (valid) {
-    const double a = alpha[col];
+    const T a = (T)alpha[col];
     for (long long i = r0 + rl; i < r1; i += 8) {
       long long e = i * g.W + col;
       X[e] = fma(a, P[e], X[e]);
-      double r = fma(-a, Q[e], R[e]);
+      T r = fma(-a, Q[e], R[e]);
       R[e] = r;
-      double z = r * inv_diag[i];
-      rz = fma(r, z, rz);
-      rr = fma(r, r, rr);
+      T z = r * (T)inv_diag[i];
+      rz.add(r, z);
+      rr.add(r, r);
     }
   }
   const long long plane = (long long)g.row_blocks * g.W;
-  cta_col_partial(rz, sh, partials, col, g.W, col < g.W);
-  cta_col_partial(rr, sh, partials + plane, col, g.W, col < g.W);
+  cta_col_partial(rz.value(), sh, partials, col, g.W, col < g.W);
+  cta_col_partial(rr.value(), sh, partials + plane, col, g.W, col < g.W);
 }
 
 __global__ void k_cg_beta(CgGeom g, const double* __restrict__ partials, double* rz,
@@ -256,55 +286,92 @@ __global__ void k_cg_beta(CgGeom g, const double* __restrict__ partials, double*
   }
 }
 
-__global__ void __launch_bounds__(kCgThreads) k_cg_dir(CgGeom g, const double* __restrict__ R,
-                                                       double* __restrict__ P,
+template <typename T>
+__global__ void __launch_bounds__(kCgThreads) k_cg_dir(CgGeom g, const T* __restrict__ R,
+                                                       T* __restrict__ P,
                                                        const double* __restrict__ inv_diag,
                                                        const double* __restrict__ beta,
                                                        const int32_t* __restrict__ done) {
   const int col = blockIdx.x * 32 + (threadIdx.x & 31);
   const int rl = threadIdx.x >> 5;
   if (col >= g.W || done[col]) return;
-  const double b = beta[col];
+  const T b = (T)beta[col];
   const long long r0 = (long long)blockIdx.y * g.rows_per_block;
   const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
   for (long long i = r0 + rl; i < r1; i += 8) {
     long long e = i * g.W + col;
-    P[e] = fma(b, P[e], R[e] * inv_diag[i]);
+    P[e] = fma(b, P[e], R[e] * (T)inv_diag[i]);
   }
 }
 
-void cg_init(const CgGeom& g, const double* B, double* X, double* R, double* P,
-             const double* inv_diag, CgState& st, cudaStream_t s, Launches& L) {
+template <typename T>
+static void cg_init_t(const CgGeom& g, const double* B, void* X, void* R, void* P,
+                      const double* inv_diag, CgState& st, cudaStream_t s, Launches& L) {
   dim3 grid((g.W + 31) / 32, g.row_blocks);
-  k_cg_init<<<grid, kCgThreads, 0, s>>>(g, B, X, R, P, inv_diag, st.partials);
+  k_cg_init<T><<<grid, kCgThreads, 0, s>>>(g, B, (T*)X, (T*)R, (T*)P, inv_diag, st.partials);
   k_cg_init_cols<<<(g.W + 7) / 8, 256, 0, s>>>(g, st.partials, st.rz, st.bb, st.done, st.iters);
   L.add(2);
 }
 
-void cg_iteration(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx,
-                  const int32_t* deg, const double* inv_d, const uint8_t* is_anchor,
-                  const double* inv_diag, int kind, double* X, double* R, double* P, double* T,
-                  double* Q, double rtol, int max_iters, CgState& st, cudaStream_t s,
-                  Launches& L, cudaEvent_t* ev) {
+void cg_init(const CgGeom& g, const double* B, void* X, void* R, void* P,
+             const double* inv_diag, CgState& st, int single, cudaStream_t s, Launches& L) {
+  if (single) cg_init_t<float>(g, B, X, R, P, inv_diag, st, s, L);
+  else cg_init_t<double>(g, B, X, R, P, inv_diag, st, s, L);
+}
+
+template <typename T>
+static void cg_iteration_t(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx,
+                           const int32_t* deg, const double* inv_d, const uint8_t* is_anchor,
+                           const double* inv_diag, int kind, T* X, T* R, T* P, T* Tv, T* Q,
+                           double rtol, int max_iters, CgState& st, cudaStream_t s, Launches& L,
+                           cudaEvent_t* ev) {
   dim3 grid((g.W + 31) / 32, g.row_blocks);
   dim3 cgrid((g.W + 7) / 8);
   if (ev) cudaEventRecord(ev[0], s);
-  k_cg_L<<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, P, T, st.done);
+  k_cg_L<T><<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, P, Tv, st.done);
   if (ev) cudaEventRecord(ev[1], s);
-  k_cg_LT<<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, is_anchor, T, P, Q,
-                                       st.done, st.partials);
+  k_cg_LT<T><<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, is_anchor, Tv, P,
+                                          Q, st.done, st.partials);
   if (ev) cudaEventRecord(ev[2], s);
   k_cg_alpha<<<cgrid, 256, 0, s>>>(g, st.partials, st.rz, st.alpha, st.done, st.active);
   if (ev) cudaEventRecord(ev[3], s);
-  k_cg_update<<<grid, kCgThreads, 0, s>>>(g, X, R, P, Q, inv_diag, st.alpha, st.done,
-                                           st.partials);
+  k_cg_update<T><<<grid, kCgThreads, 0, s>>>(g, X, R, P, Q, inv_diag, st.alpha, st.done,
+                                              st.partials);
   if (ev) cudaEventRecord(ev[4], s);
   k_cg_beta<<<cgrid, 256, 0, s>>>(g, st.partials, st.rz, st.rr, st.bb, st.beta, st.done,
                                   st.iters, rtol * rtol, max_iters, st.active);
   if (ev) cudaEventRecord(ev[5], s);
-  k_cg_dir<<<grid, kCgThreads, 0, s>>>(g, R, P, inv_diag, st.beta, st.done);
+  k_cg_dir<T><<<grid, kCgThreads, 0, s>>>(g, R, P, inv_diag, st.beta, st.done);
   if (ev) cudaEventRecord(ev[6], s);
   L.add(6);
+}
+
+void cg_iteration(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx,
+                  const int32_t* deg, const double* inv_d, const uint8_t* is_anchor,
+                  const double* inv_diag, int kind, void* X, void* R, void* P, void* T, void* Q,
+                  double rtol, int max_iters, CgState& st, int single, cudaStream_t s,
+                  Launches& L, cudaEvent_t* ev) {
+  if (single)
+    cg_iteration_t<float>(g, row_ptr, col_idx, deg, inv_d, is_anchor, inv_diag, kind, (float*)X,
+                          (float*)R, (float*)P, (float*)T, (float*)Q, rtol, max_iters, st, s, L,
+                          ev);
+  else
+    cg_iteration_t<double>(g, row_ptr, col_idx, deg, inv_d, is_anchor, inv_diag, kind,
+                           (double*)X, (double*)R, (double*)P, (double*)T, (double*)Q, rtol,
+                           max_iters, st, s, L, ev);
+}
+
+// out[e] = (double) X[e]
+__global__ void k_widen(const float* __restrict__ X, long long count, double* __restrict__ out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = (double)X[e];
+}
+
+void widen(const float* X, long long count, double* out, cudaStream_t s, Launches& L) {
+  int grid = (int)std::min<long long>((count + 255) / 256, 152 * 32);
+  k_widen<<<std::max(grid, 1), 256, 0, s>>>(X, count, out);
+  L.add(1);
 }
 
 const char* const kCgKernelNames[kCgKernels] = {"k_cg_L", "k_cg_LT", "k_cg_alpha",

@@ -1,0 +1,69 @@
+// The codec handle (opaque in the C ABI), shared by the translation units
+// that enqueue the encoder and decoder.
+#pragma once
+
+#include <vector>
+
+#include "mc_internal.cuh"
+
+struct mesh_codec {
+  mesh_codec_params_t p;
+  int n, T, F, k, W, n_c, kind;
+  mc::EncodeLayout lay;
+  mc::CgGeom geom;
+  // device workspace (one allocation)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  int32_t *row_ptr, *col_idx, *deg, *anchors, *dec_anchors;
+  uint8_t* is_anchor;
+  double *inv_d, *inv_diag;
+  double *Q0, *Q, *Zb, *U, *V, *H, *theta, *Wk, *partials, *chg_work, *chg;
+  double *G, *Rf;
+  double *Cf, *qparams;
+  double *X, *D, *B, *R, *P, *Tv, *Qv;
+  double *Udeq, *Cdeq, *Ahat;
+  mc::CgState cg;
+  uint32_t* d_status;
+  int nnz;
+  size_t partial_elems;
+  // host side
+  uint32_t* h_status = nullptr;     // pinned
+  int32_t* h_active = nullptr;      // pinned
+  uint8_t* h_header = nullptr;      // pinned, 64 bytes
+  double* h_chg = nullptr;          // pinned [3]
+  // staging for the host-buffer entry points (lazy)
+  double* stage_pos = nullptr;
+  uint8_t* stage_bits = nullptr;
+  cudaStream_t last_stream = nullptr;
+  uint64_t launches_create = 0, launches_encode = 0, launches_decode = 0;
+  int oi_done[3] = {0, 0, 0};
+  double oi_last_change[3] = {0, 0, 0};
+  int cg_columns = 0;
+  // kernel timing (mesh_codec_set_profiling)
+  int prof_every = 0;
+  std::vector<cudaEvent_t> prof_events;   // groups of kCgKernels + 1
+  size_t prof_used = 0;                    // groups recorded in the current decode
+  int64_t prof_launches[MESH_CODEC_PROF_KERNELS] = {0};
+  double prof_ms[MESH_CODEC_PROF_KERNELS] = {0};
+  // mixed precision (precision TF32 / BF16): tensor-core operands and maps
+  int lp = -1;                      // 0 tf32 (FP32 storage), 1 bf16; -1 FP64 mode
+  int Fp = 0, kp = 0, np = 0;       // frames, rank, vertices padded for TMA boxes
+  void *Xlp = nullptr, *XTlp = nullptr, *Dlp = nullptr, *Qtlp = nullptr, *Wtlp = nullptr;
+  void *Utlp = nullptr, *Clp = nullptr, *Ulp = nullptr;
+  float* tc_part = nullptr;         // split-K partial products
+  double* Zfull = nullptr;          // [3][Fp][kp]
+  size_t tc_part_elems = 0;
+  alignas(64) unsigned char map_X[128], map_Qt[128], map_XT[128], map_Wt[128];
+  alignas(64) unsigned char map_D[128], map_Ut[128], map_C[128], map_U[128];
+  int refine_sweeps = 0;
+};
+
+namespace mc {
+// mixed-precision helpers (mc_mixed.cu)
+void mixed_dims(mesh_codec* h);
+size_t mixed_carve(mesh_codec* h, char* base, size_t off);
+bool mixed_init(mesh_codec* h, cudaStream_t s);
+void mixed_oi_sweeps(mesh_codec* h, int sweeps, cudaStream_t s, Launches& L);
+void mixed_project(mesh_codec* h, cudaStream_t s, Launches& L);
+void mixed_backproject(mesh_codec* h, cudaStream_t s, Launches& L);
+}  // namespace mc

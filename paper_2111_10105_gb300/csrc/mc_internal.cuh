@@ -118,8 +118,10 @@ bool tc_operand_map(void* map_out, const void* base, int elem_bytes, long long K
 inline int tc_bn(int N) { return N <= 256 ? ((N + 15) / 16) * 16 : 256; }
 size_t tc_smem_bytes(int BN);
 // D = A B^T (FP32 accumulate) on tcgen05; kind 0 tf32, 1 bf16; returns splits used
+// out_kind: 0 fp32, 1 fp32 rounded to tf32, 2 bf16, 3 fp64; element (m, n) of
+// batch b / split z at out[b*sb + z*split_stride + m*s0 + n*s1]
 int umma_tn(int kind, const void* mapA, const void* mapB, int M, int N, int K, int batch,
-            int splits, float* out, long long s0, long long s1, long long sb,
+            int splits, void* out, int out_kind, long long s0, long long s1, long long sb,
             long long split_stride, uint32_t* status, cudaStream_t s, Launches& L);
 void pack_operand_f64(const double* src, long long ssb, long long sr, long long sc, int batch,
                       long long rows, long long cols, long long dcols, long long dpitch,
@@ -175,13 +177,15 @@ struct CgGeom {
 };
 CgGeom cg_geometry(int n, int W);
 size_t cg_partials_elems(int n, int W);
-void cg_init(const CgGeom& g, const double* B, double* X, double* R, double* P,
-             const double* inv_diag, CgState& st, cudaStream_t s, Launches& L);
+// vectors X, R, P, T, Q are double (single = 0) or float (single = 1) [n][W]
+void cg_init(const CgGeom& g, const double* B, void* X, void* R, void* P,
+             const double* inv_diag, CgState& st, int single, cudaStream_t s, Launches& L);
 void cg_iteration(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx,
                   const int32_t* deg, const double* inv_d, const uint8_t* is_anchor,
-                  const double* inv_diag, int kind, double* X, double* R, double* P, double* T,
-                  double* Q, double rtol, int max_iters, CgState& st, cudaStream_t s,
+                  const double* inv_diag, int kind, void* X, void* R, void* P, void* T, void* Q,
+                  double rtol, int max_iters, CgState& st, int single, cudaStream_t s,
                   Launches& L, cudaEvent_t* ev /* 7 events around the 6 kernels, or null */);
+void widen(const float* X, long long count, double* out, cudaStream_t s, Launches& L);
 constexpr int kCgKernels = 6;
 extern const char* const kCgKernelNames[kCgKernels];
 void scatter_anchor_rhs(double* B, const double* Ahat, const int32_t* anchors, int n_c, int F,

@@ -95,7 +95,8 @@ struct Args {
   int M, N, K;
   int BN, tmem_cols;
   int batch, splits, chunks_per_split, total_chunks;
-  float* out;
+  void* out;
+  int out_kind;   // 0 fp32, 1 fp32 rounded to tf32, 2 bf16, 3 fp64
   long long s0, s1, sb, split_stride;
   uint32_t* status;
 };
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(128, 1) k_umma_tn(const __grid_constant__ CUte
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {
     const int row = warp * 32 + lane, m = m0 + row;
-    float* outb = a.out + (long long)b * a.sb + (long long)split * a.split_stride;
+    const long long base = (long long)b * a.sb + (long long)split * a.split_stride;
     for (int c = 0; c < a.BN; c += 16) {
       uint32_t r[16];
       const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
@@ -220,7 +221,21 @@ __global__ void __launch_bounds__(128, 1) k_umma_tn(const __grid_constant__ CUte
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int n = n0 + c + j;
-          if (n < a.N) outb[(long long)m * a.s0 + (long long)n * a.s1] = __uint_as_float(r[j]);
+          if (n < a.N) {
+            const long long o = base + (long long)m * a.s0 + (long long)n * a.s1;
+            const float v = __uint_as_float(r[j]);
+            if (a.out_kind == 0) {
+              ((float*)a.out)[o] = v;
+            } else if (a.out_kind == 1) {
+              uint32_t t;
+              asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
+              ((float*)a.out)[o] = __uint_as_float(t);
+            } else if (a.out_kind == 2) {
+              ((__nv_bfloat16*)a.out)[o] = __float2bfloat16_rn(v);
+            } else {
+              ((double*)a.out)[o] = (double)v;
+            }
+          }
         }
       }
     }
@@ -295,7 +310,7 @@ size_t tc_smem_bytes(int BN) {
 // out + b*sb + z*split_stride + m*s0 + n*s1.  kind: 0 tf32, 1 bf16.
 // Returns the number of K splits used (each writes its own partial).
 int umma_tn(int kind, const void* mapA, const void* mapB, int M, int N, int K, int batch,
-            int splits, float* out, long long s0, long long s1, long long sb,
+            int splits, void* out, int out_kind, long long s0, long long s1, long long sb,
             long long split_stride, uint32_t* status, cudaStream_t s, Launches& L) {
   const int atom = kind == 0 ? 32 : 64;
   int BN = N <= 256 ? ((N + 15) / 16) * 16 : 256;
@@ -307,7 +322,7 @@ int umma_tn(int kind, const void* mapA, const void* mapB, int M, int N, int K, i
   if (splits < 1) splits = 1;
   a.chunks_per_split = (a.total_chunks + splits - 1) / splits;
   a.splits = (a.total_chunks + a.chunks_per_split - 1) / a.chunks_per_split;
-  a.out = out; a.s0 = s0; a.s1 = s1; a.sb = sb; a.split_stride = split_stride;
+  a.out = out; a.out_kind = out_kind; a.s0 = s0; a.s1 = s1; a.sb = sb; a.split_stride = split_stride;
   a.status = status;
   const size_t sm = tc_smem_bytes(BN);
   dim3 grid((N + BN - 1) / BN, (M + tc::kBM - 1) / tc::kBM, batch * a.splits);
@@ -425,7 +440,8 @@ extern "C" mesh_codec_status_t mesh_codec_selftest_gemm(int kind, int M, int N, 
     st = MC_E_CUDA;
     goto out;
   }
-  used = umma_tn(kind, ma, mb, M, N, K, 1, splits, part, N, 1, 0, (long long)M * N, status, s, L);
+  used = umma_tn(kind, ma, mb, M, N, K, 1, splits, part, 0, N, 1, 0, (long long)M * N, status, s,
+                 L);
   sum_splits(part, used, (long long)M * N, (long long)M * N, C, s, L);
   {
     uint32_t bits = 0;

@@ -18,6 +18,7 @@ WORKLOADS = {
     # name: (sweeps, frames or None for all)
     "icosphere4_F64_k16": (30, None),
     "torus200x100_F256_k32": (30, None),
+    "grid316_F512_k64": (30, None),
 }
 
 

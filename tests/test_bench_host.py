@@ -1,0 +1,74 @@
+"""Host logic of bench.py: throughput aggregation over ranks (gloo, world
+size 2, on CPU), clock-record parsing and the roofline arithmetic."""
+
+import os
+import socket
+
+import pytest
+
+import bench
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # rank r processed (r + 1) * 1000 vertex-frames in (r + 1) seconds
+    v, t = bench.aggregate((rank + 1) * 1000.0, float(rank + 1), world, dist)
+    q.put((rank, v, t))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_aggregate_two_ranks_gloo():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    for _, v, t in res:
+        assert t == 2.0                     # max over ranks
+        assert v == pytest.approx(3000.0 / 2.0)   # all vertex-frames / slowest time
+
+
+def test_aggregate_single_rank():
+    assert bench.aggregate(500.0, 2.0, 1) == (250.0, 2.0)
+
+
+def test_parse_clock_rows():
+    text = ("0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+            "0, 1980, 2070, 1300.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n"
+            "0, 2070, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    r = bench.parse_clock_rows(text)
+    assert r["sm_mhz"] == 2070 and r["sm_max_mhz"] == 2070 and r["samples"] == 3
+    assert r["reasons"] == ["sw_power_cap"]
+
+
+def test_roofline_arithmetic():
+    prof = {"k_cg_L": (10, 2.0), "k_cg_LT": (10, 3.0), "k_cg_update": (10, 1.0),
+            "k_cg_dir": (10, 0.5), "k_cg_alpha": (10, 0.1), "k_cg_beta": (10, 0.1)}
+    stats = {"cg_iters_mean": 100.0, "cg_iters_max": 100}
+    n, W, nnz, n_c = 1000000, 64, 6000000, 10
+    r = bench.roofline(prof, stats, n, W, nnz, n_c, {"hbm_gbs": 6756.5}, single=False)
+    assert r["kernel"] == "k_cg_LT" and r["bound"] == "alu"
+    flops = n * W * (2 * 6 + 3) + n_c * W
+    assert r["achieved"] == pytest.approx(flops / 0.3e-3 / 1e12, rel=1e-3)
+    r = bench.roofline(prof, stats, n, W, nnz, n_c, {"hbm_gbs": 6756.5}, single=True)
+    nbytes = n * W * 3 * 4 + 4 * (n + 1) + 4 * nnz + 9 * n
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(nbytes / 0.3e-3 / 1e9, rel=1e-3)
+    assert abs(sum(r["time_share"].values()) - 1.0) < 1e-3
