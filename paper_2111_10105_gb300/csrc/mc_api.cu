@@ -50,6 +50,8 @@ size_t carve(mesh_codec* h, void* base) {
   h->is_anchor = c.take<uint8_t>(n);
   h->inv_d = c.take<double>(n);
   h->inv_diag = c.take<double>(n);
+  h->inv_d32 = c.take<float>(n);
+  h->inv_diag32 = c.take<float>(n);
   h->Q0 = c.take<double>(3 * F * k);
   h->Q = c.take<double>(3 * F * k);
   h->Zb = c.take<double>(3 * F * k);
@@ -507,16 +509,24 @@ static mesh_codec_status_t enqueue_decode(mesh_codec* h, const uint8_t* in, doub
   }
   // CG: FP64 vectors, or FP32 vectors with FP64 dot products in the mixed modes
   const int single = h->lp >= 0 ? 1 : 0;
-  cg_init(geom, h->B, h->X, h->R, h->P, h->inv_diag, h->cg, single, s, L);
+  const void* inv_d = h->inv_d;
+  const void* inv_diag = h->inv_diag;
+  if (single) {   // FP32 copies: no FP64 conversions in the FP32 kernels
+    narrow(h->inv_d, n, h->inv_d32, s, L);
+    narrow(h->inv_diag, n, h->inv_diag32, s, L);
+    inv_d = h->inv_d32;
+    inv_diag = h->inv_diag32;
+  }
+  cg_init(geom, h->B, h->X, h->R, h->P, inv_diag, h->cg, single, s, L);
   h->cg_columns = Wc;
   const int batch = 32;
   int it = 0;
   while (it < h->p.cg_max_iters) {
     int m = std::min(batch, h->p.cg_max_iters - it);
     for (int j = 0; j < m; ++j)
-      cg_iteration(geom, h->row_ptr, h->col_idx, h->deg, h->inv_d, h->is_anchor, h->inv_diag,
-                   h->kind, h->X, h->R, h->P, h->Tv, h->Qv, h->p.cg_rtol, h->p.cg_max_iters, h->cg,
-                   single, s, L, prof_group(h, it + j));
+      cg_iteration(geom, h->row_ptr, h->col_idx, h->deg, inv_d, h->is_anchor, inv_diag, h->kind,
+                   h->X, h->R, h->P, h->Tv, h->Qv, h->p.cg_rtol, h->p.cg_max_iters, h->cg, single,
+                   s, L, prof_group(h, it + j));
     it += m;
     MC_TRY(cudaMemcpyAsync(h->h_active, h->cg.active, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     MC_TRY(cudaStreamSynchronize(s));

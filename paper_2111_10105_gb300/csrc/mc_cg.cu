@@ -93,7 +93,7 @@ template <typename T>
 __global__ void __launch_bounds__(kCgThreads) k_cg_init(CgGeom g, const double* __restrict__ B,
                                                         T* __restrict__ X, T* __restrict__ R,
                                                         T* __restrict__ P,
-                                                        const double* __restrict__ inv_diag,
+                                                        const T* __restrict__ inv_diag,
                                                         double* __restrict__ partials) {
   __shared__ double sh[256];
   const int col = blockIdx.x * 32 + (threadIdx.x & 31);
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_init(CgGeom g, const double* 
     for (long long i = r0 + rl; i < r1; i += 8) {
       long long e = i * g.W + col;
       const T b = (T)B[e];
-      const T z = b * (T)inv_diag[i];
+      const T z = b * inv_diag[i];
       X[e] = (T)0;
       R[e] = b;
       P[e] = z;
@@ -150,7 +150,7 @@ template <typename T>
 __global__ void __launch_bounds__(kCgThreads) k_cg_L(CgGeom g, const int32_t* __restrict__ row_ptr,
                                                      const int32_t* __restrict__ col_idx,
                                                      const int32_t* __restrict__ deg,
-                                                     const double* __restrict__ inv_d, int kind,
+                                                     const T* __restrict__ inv_d, int kind,
                                                      const T* __restrict__ P, T* __restrict__ Tv,
                                                      const int32_t* __restrict__ done) {
   const int col = blockIdx.x * 32 + (threadIdx.x & 31);
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_L(CgGeom g, const int32_t* __
     T acc = (T)0;
     for (int p = b; p < e; ++p) acc += P[(long long)col_idx[p] * g.W + col];
     T pi = P[i * g.W + col];
-    Tv[i * g.W + col] = (kind == 0) ? fma(-(T)inv_d[i], acc, pi) : fma((T)deg[i], pi, -acc);
+    Tv[i * g.W + col] = (kind == 0) ? fma(-inv_d[i], acc, pi) : fma((T)deg[i], pi, -acc);
   }
 }
 
@@ -172,7 +172,7 @@ template <typename T>
 __global__ void __launch_bounds__(kCgThreads) k_cg_LT(CgGeom g, const int32_t* __restrict__ row_ptr,
                                                       const int32_t* __restrict__ col_idx,
                                                       const int32_t* __restrict__ deg,
-                                                      const double* __restrict__ inv_d, int kind,
+                                                      const T* __restrict__ inv_d, int kind,
                                                       const uint8_t* __restrict__ is_anchor,
                                                       const T* __restrict__ Tv,
                                                       const T* __restrict__ P, T* __restrict__ Q,
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_LT(CgGeom g, const int32_t* _
       if (kind == 0) {
         for (int p = b; p < e; ++p) {
           int i = col_idx[p];
-          acc = fma((T)inv_d[i], Tv[(long long)i * g.W + col], acc);
+          acc = fma(inv_d[i], Tv[(long long)i * g.W + col], acc);
         }
       } else {
         for (int p = b; p < e; ++p) acc += Tv[(long long)col_idx[p] * g.W + col];
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_update(CgGeom g, T* __restric
                                                           T* __restrict__ R,
                                                           const T* __restrict__ P,
                                                           const T* __restrict__ Q,
-                                                          const double* __restrict__ inv_diag,
+                                                          const T* __restrict__ inv_diag,
                                                           const double* __restrict__ alpha,
                                                           const int32_t* __restrict__ done,
                                                           double* __restrict__ partials) {
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_update(CgGeom g, T* __restric
       X[e] = fma(a, P[e], X[e]);
       T r = fma(-a, Q[e], R[e]);
       R[e] = r;
-      T z = r * (T)inv_diag[i];
+      T z = r * inv_diag[i];
       rz.add(r, z);
       rr.add(r, r);
     }
@@ -289,7 +289,7 @@ __global__ void k_cg_beta(CgGeom g, const double* __restrict__ partials, double*
 template <typename T>
 __global__ void __launch_bounds__(kCgThreads) k_cg_dir(CgGeom g, const T* __restrict__ R,
                                                        T* __restrict__ P,
-                                                       const double* __restrict__ inv_diag,
+                                                       const T* __restrict__ inv_diag,
                                                        const double* __restrict__ beta,
                                                        const int32_t* __restrict__ done) {
   const int col = blockIdx.x * 32 + (threadIdx.x & 31);
@@ -300,29 +300,30 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_dir(CgGeom g, const T* __rest
   const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
   for (long long i = r0 + rl; i < r1; i += 8) {
     long long e = i * g.W + col;
-    P[e] = fma(b, P[e], R[e] * (T)inv_diag[i]);
+    P[e] = fma(b, P[e], R[e] * inv_diag[i]);
   }
 }
 
 template <typename T>
 static void cg_init_t(const CgGeom& g, const double* B, void* X, void* R, void* P,
-                      const double* inv_diag, CgState& st, cudaStream_t s, Launches& L) {
+                      const void* inv_diag, CgState& st, cudaStream_t s, Launches& L) {
   dim3 grid((g.W + 31) / 32, g.row_blocks);
-  k_cg_init<T><<<grid, kCgThreads, 0, s>>>(g, B, (T*)X, (T*)R, (T*)P, inv_diag, st.partials);
+  k_cg_init<T><<<grid, kCgThreads, 0, s>>>(g, B, (T*)X, (T*)R, (T*)P, (const T*)inv_diag,
+                                           st.partials);
   k_cg_init_cols<<<(g.W + 7) / 8, 256, 0, s>>>(g, st.partials, st.rz, st.bb, st.done, st.iters);
   L.add(2);
 }
 
 void cg_init(const CgGeom& g, const double* B, void* X, void* R, void* P,
-             const double* inv_diag, CgState& st, int single, cudaStream_t s, Launches& L) {
+             const void* inv_diag, CgState& st, int single, cudaStream_t s, Launches& L) {
   if (single) cg_init_t<float>(g, B, X, R, P, inv_diag, st, s, L);
   else cg_init_t<double>(g, B, X, R, P, inv_diag, st, s, L);
 }
 
 template <typename T>
 static void cg_iteration_t(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx,
-                           const int32_t* deg, const double* inv_d, const uint8_t* is_anchor,
-                           const double* inv_diag, int kind, T* X, T* R, T* P, T* Tv, T* Q,
+                           const int32_t* deg, const T* inv_d, const uint8_t* is_anchor,
+                           const T* inv_diag, int kind, T* X, T* R, T* P, T* Tv, T* Q,
                            double rtol, int max_iters, CgState& st, cudaStream_t s, Launches& L,
                            cudaEvent_t* ev) {
   dim3 grid((g.W + 31) / 32, g.row_blocks);
@@ -347,16 +348,18 @@ static void cg_iteration_t(const CgGeom& g, const int32_t* row_ptr, const int32_
 }
 
 void cg_iteration(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx,
-                  const int32_t* deg, const double* inv_d, const uint8_t* is_anchor,
-                  const double* inv_diag, int kind, void* X, void* R, void* P, void* T, void* Q,
+                  const int32_t* deg, const void* inv_d, const uint8_t* is_anchor,
+                  const void* inv_diag, int kind, void* X, void* R, void* P, void* T, void* Q,
                   double rtol, int max_iters, CgState& st, int single, cudaStream_t s,
                   Launches& L, cudaEvent_t* ev) {
   if (single)
-    cg_iteration_t<float>(g, row_ptr, col_idx, deg, inv_d, is_anchor, inv_diag, kind, (float*)X,
+    cg_iteration_t<float>(g, row_ptr, col_idx, deg, (const float*)inv_d, is_anchor,
+                          (const float*)inv_diag, kind, (float*)X,
                           (float*)R, (float*)P, (float*)T, (float*)Q, rtol, max_iters, st, s, L,
                           ev);
   else
-    cg_iteration_t<double>(g, row_ptr, col_idx, deg, inv_d, is_anchor, inv_diag, kind,
+    cg_iteration_t<double>(g, row_ptr, col_idx, deg, (const double*)inv_d, is_anchor,
+                           (const double*)inv_diag, kind,
                            (double*)X, (double*)R, (double*)P, (double*)T, (double*)Q, rtol,
                            max_iters, st, s, L, ev);
 }
@@ -366,6 +369,19 @@ __global__ void k_widen(const float* __restrict__ X, long long count, double* __
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
        e += (long long)gridDim.x * blockDim.x)
     out[e] = (double)X[e];
+}
+
+// out[e] = (float) X[e]
+__global__ void k_narrow(const double* __restrict__ X, long long count, float* __restrict__ out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = (float)X[e];
+}
+
+void narrow(const double* X, long long count, float* out, cudaStream_t s, Launches& L) {
+  int grid = (int)std::min<long long>((count + 255) / 256, 152 * 32);
+  k_narrow<<<std::max(grid, 1), 256, 0, s>>>(X, count, out);
+  L.add(1);
 }
 
 void widen(const float* X, long long count, double* out, cudaStream_t s, Launches& L) {

@@ -17,6 +17,7 @@ struct mesh_codec {
   int32_t *row_ptr, *col_idx, *deg, *anchors, *dec_anchors;
   uint8_t* is_anchor;
   double *inv_d, *inv_diag;
+  float *inv_d32, *inv_diag32;     // FP32 copies for the mixed-precision CG
   double *Q0, *Q, *Zb, *U, *V, *H, *theta, *Wk, *partials, *chg_work, *chg;
   double *G, *Rf;
   double *Cf, *qparams;

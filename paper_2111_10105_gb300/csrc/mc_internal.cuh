@@ -178,14 +178,16 @@ struct CgGeom {
 CgGeom cg_geometry(int n, int W);
 size_t cg_partials_elems(int n, int W);
 // vectors X, R, P, T, Q are double (single = 0) or float (single = 1) [n][W]
+// inv_d, inv_diag: double (single = 0) or float (single = 1) [n]
 void cg_init(const CgGeom& g, const double* B, void* X, void* R, void* P,
-             const double* inv_diag, CgState& st, int single, cudaStream_t s, Launches& L);
+             const void* inv_diag, CgState& st, int single, cudaStream_t s, Launches& L);
 void cg_iteration(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx,
-                  const int32_t* deg, const double* inv_d, const uint8_t* is_anchor,
-                  const double* inv_diag, int kind, void* X, void* R, void* P, void* T, void* Q,
+                  const int32_t* deg, const void* inv_d, const uint8_t* is_anchor,
+                  const void* inv_diag, int kind, void* X, void* R, void* P, void* T, void* Q,
                   double rtol, int max_iters, CgState& st, int single, cudaStream_t s,
                   Launches& L, cudaEvent_t* ev /* 7 events around the 6 kernels, or null */);
 void widen(const float* X, long long count, double* out, cudaStream_t s, Launches& L);
+void narrow(const double* X, long long count, float* out, cudaStream_t s, Launches& L);
 constexpr int kCgKernels = 6;
 extern const char* const kCgKernelNames[kCgKernels];
 void scatter_anchor_rhs(double* B, const double* Ahat, const int32_t* anchors, int n_c, int F,
