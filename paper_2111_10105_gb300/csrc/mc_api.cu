@@ -211,7 +211,7 @@ static mesh_codec_status_t create_impl(mesh_codec* h, const int32_t* tris_in, in
   const int n = h->n, T = h->T;
   h->lay = make_layout(n, h->F, h->k, h->n_c, h->p.coeff_bits, h->p.dict_bits,
                        h->p.anchor_bits, h->kind);
-  h->geom = cg_geometry(n, h->W);
+  h->geom = cg_geometry(n, h->W, 0);
   // split-K partial buffer: the largest of the encoder's reductions
   {
     size_t F = h->F, k = h->k;
@@ -294,6 +294,10 @@ static mesh_codec_status_t create_impl(mesh_codec* h, const int32_t* tris_in, in
   if (st == MC_OK) {
     cudaMemcpy(&nnz, h->row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost);
     h->nnz = nnz;
+    std::vector<int32_t> dg(n);
+    cudaMemcpy(dg.data(), h->deg, sizeof(int32_t) * n, cudaMemcpyDeviceToHost);
+    h->max_degree = 0;
+    for (int i = 0; i < n; ++i) h->max_degree = std::max(h->max_degree, (int)dg[i]);
   }
   cudaFree(tmp);
   if (st == MC_OK) MC_TRY(cudaGetLastError());
@@ -485,7 +489,7 @@ static mesh_codec_status_t enqueue_decode(mesh_codec* h, const uint8_t* in, doub
   const bool factored = use_factored(h);
   // CG columns: 3F frames (Eq. 11-12 as written), or 3k + n_c factored columns
   const int Wc = factored ? 3 * k + h->n_c : W;
-  const CgGeom geom = cg_geometry(n, Wc);
+  const CgGeom geom = cg_geometry(n, Wc, h->max_degree);
   if (!factored) {
     // delta~_c = (U_c' C_c')^T : (n x k)(k x F) into D[:, cF : cF + F]
     if (h->lp >= 0) {

@@ -26,7 +26,7 @@ namespace mc {
 
 static constexpr int kCgThreads = 256;  // 32 columns x 8 row lanes
 
-CgGeom cg_geometry(int n, int W) {
+CgGeom cg_geometry(int n, int W, int max_degree) {
   CgGeom g{};
   g.n = n;
   g.W = W;
@@ -36,11 +36,14 @@ CgGeom cg_geometry(int n, int W) {
   rpb = std::max(8, (rpb + 7) / 8 * 8);
   g.rows_per_block = rpb;
   g.row_blocks = (n + rpb - 1) / rpb;
+  // shared-memory CSR slice: row offsets + at most rows * max_degree indices
+  long long ints = (long long)rpb + 1 + (long long)rpb * std::max(max_degree, 0);
+  g.slice_ints = (max_degree > 0 && ints * 4 <= kCgSliceBytes) ? (int)ints : 0;
   return g;
 }
 
 size_t cg_partials_elems(int n, int W) {
-  CgGeom g = cg_geometry(n, W);
+  CgGeom g = cg_geometry(n, W, 0);
   return (size_t)g.row_blocks * W * 2;
 }
 
@@ -145,6 +148,73 @@ __global__ void k_cg_init_cols(CgGeom g, const double* __restrict__ partials, do
   }
 }
 
+// The CSR slice of a CTA's row block (relative row offsets, then column
+// indices) is staged in shared memory once per launch when it fits
+// (g.slice_ints > 0): every row then costs one dependent global load (the
+// neighbours' values) instead of three.  Neighbour values are loaded four at
+// a time and summed in ascending order, the same order as one at a time.
+struct CsrView {
+  const int32_t* rp;   // row offsets, indexed by row - r0
+  const int32_t* ci;   // column indices, indexed by the offsets in rp
+};
+
+__device__ __forceinline__ CsrView stage_csr(const CgGeom& g, const int32_t* __restrict__ row_ptr,
+                                             const int32_t* __restrict__ col_idx, long long r0,
+                                             long long r1, int32_t* smem) {
+  if (g.slice_ints <= 0) return CsrView{row_ptr + r0, col_idx};
+  const int nrows = (int)(r1 - r0);
+  const int base = row_ptr[r0];
+  const int nnz_s = row_ptr[r1] - base;
+  int32_t* s_rp = smem;
+  int32_t* s_ci = smem + g.rows_per_block + 1;
+  for (int t = threadIdx.x; t <= nrows; t += blockDim.x) s_rp[t] = row_ptr[r0 + t] - base;
+  for (int t = threadIdx.x; t < nnz_s; t += blockDim.x) s_ci[t] = col_idx[base + t];
+  __syncthreads();
+  return CsrView{s_rp, s_ci};
+}
+
+// sum over p in [b, e) of V[ci[p]*W + col], ascending p
+template <typename T>
+__device__ __forceinline__ T gather_sum(const T* __restrict__ V, const int32_t* ci, int b, int e,
+                                        int W, int col) {
+  T acc = (T)0;
+  int p = b;
+  for (; p + 4 <= e; p += 4) {
+    const int c0 = ci[p], c1 = ci[p + 1], c2 = ci[p + 2], c3 = ci[p + 3];
+    const T v0 = V[(long long)c0 * W + col], v1 = V[(long long)c1 * W + col];
+    const T v2 = V[(long long)c2 * W + col], v3 = V[(long long)c3 * W + col];
+    acc += v0;
+    acc += v1;
+    acc += v2;
+    acc += v3;
+  }
+  for (; p < e; ++p) acc += V[(long long)ci[p] * W + col];
+  return acc;
+}
+
+// sum over p in [b, e) of w[ci[p]] * V[ci[p]*W + col] as an FMA chain, ascending p
+template <typename T>
+__device__ __forceinline__ T gather_wsum(const T* __restrict__ V, const T* __restrict__ w,
+                                         const int32_t* ci, int b, int e, int W, int col) {
+  T acc = (T)0;
+  int p = b;
+  for (; p + 4 <= e; p += 4) {
+    const int c0 = ci[p], c1 = ci[p + 1], c2 = ci[p + 2], c3 = ci[p + 3];
+    const T v0 = V[(long long)c0 * W + col], v1 = V[(long long)c1 * W + col];
+    const T v2 = V[(long long)c2 * W + col], v3 = V[(long long)c3 * W + col];
+    const T w0 = w[c0], w1 = w[c1], w2 = w[c2], w3 = w[c3];
+    acc = fma(w0, v0, acc);
+    acc = fma(w1, v1, acc);
+    acc = fma(w2, v2, acc);
+    acc = fma(w3, v3, acc);
+  }
+  for (; p < e; ++p) {
+    const int c = ci[p];
+    acc = fma(w[c], V[(long long)c * W + col], acc);
+  }
+  return acc;
+}
+
 // T = L P for active columns
 template <typename T>
 __global__ void __launch_bounds__(kCgThreads) k_cg_L(CgGeom g, const int32_t* __restrict__ row_ptr,
@@ -153,16 +223,17 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_L(CgGeom g, const int32_t* __
                                                      const T* __restrict__ inv_d, int kind,
                                                      const T* __restrict__ P, T* __restrict__ Tv,
                                                      const int32_t* __restrict__ done) {
+  extern __shared__ int32_t s_csr[];
   const int col = blockIdx.x * 32 + (threadIdx.x & 31);
   const int rl = threadIdx.x >> 5;
-  if (col >= g.W || done[col]) return;
   const long long r0 = (long long)blockIdx.y * g.rows_per_block;
   const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
+  const CsrView v = stage_csr(g, row_ptr, col_idx, r0, r1, s_csr);
+  if (col >= g.W || done[col]) return;
   for (long long i = r0 + rl; i < r1; i += 8) {
-    int b = row_ptr[i], e = row_ptr[i + 1];
-    T acc = (T)0;
-    for (int p = b; p < e; ++p) acc += P[(long long)col_idx[p] * g.W + col];
-    T pi = P[i * g.W + col];
+    const int b = v.rp[i - r0], e = v.rp[i - r0 + 1];
+    const T acc = gather_sum(P, v.ci, b, e, g.W, col);
+    const T pi = P[i * g.W + col];
     Tv[i * g.W + col] = (kind == 0) ? fma(-inv_d[i], acc, pi) : fma((T)deg[i], pi, -acc);
   }
 }
@@ -178,28 +249,23 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_LT(CgGeom g, const int32_t* _
                                                       const T* __restrict__ P, T* __restrict__ Q,
                                                       const int32_t* __restrict__ done,
                                                       double* __restrict__ partials) {
+  extern __shared__ int32_t s_csr[];
   __shared__ double sh[256];
   const int col = blockIdx.x * 32 + (threadIdx.x & 31);
   const int rl = threadIdx.x >> 5;
-  const bool valid = col < g.W && !done[col];
   const long long r0 = (long long)blockIdx.y * g.rows_per_block;
   const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
+  const CsrView v = stage_csr(g, row_ptr, col_idx, r0, r1, s_csr);
+  const bool valid = col < g.W && !done[col];
   DotAcc<T> pap;
   if (valid) {
     for (long long j = r0 + rl; j < r1; j += 8) {
-      int b = row_ptr[j], e = row_ptr[j + 1];
-      T acc = (T)0;
-      if (kind == 0) {
-        for (int p = b; p < e; ++p) {
-          int i = col_idx[p];
-          acc = fma(inv_d[i], Tv[(long long)i * g.W + col], acc);
-        }
-      } else {
-        for (int p = b; p < e; ++p) acc += Tv[(long long)col_idx[p] * g.W + col];
-      }
-      T tj = Tv[j * g.W + col];
+      const int b = v.rp[j - r0], e = v.rp[j - r0 + 1];
+      const T acc = (kind == 0) ? gather_wsum(Tv, inv_d, v.ci, b, e, g.W, col)
+                                : gather_sum(Tv, v.ci, b, e, g.W, col);
+      const T tj = Tv[j * g.W + col];
       T q = (kind == 0) ? tj - acc : fma((T)deg[j], tj, -acc);
-      T pj = P[j * g.W + col];
+      const T pj = P[j * g.W + col];
       if (is_anchor[j]) q += pj;
       Q[j * g.W + col] = q;
       pap.add(pj, q);
@@ -329,9 +395,16 @@ static void cg_iteration_t(const CgGeom& g, const int32_t* row_ptr, const int32_
   dim3 grid((g.W + 31) / 32, g.row_blocks);
   dim3 cgrid((g.W + 7) / 8);
   if (ev) cudaEventRecord(ev[0], s);
-  k_cg_L<T><<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, P, Tv, st.done);
+  const size_t sm = g.slice_ints > 0 ? sizeof(int32_t) * (size_t)g.slice_ints : 0;
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[sizeof(T) == 4]) {
+    cudaFuncSetAttribute(k_cg_L<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCgSliceBytes);
+    cudaFuncSetAttribute(k_cg_LT<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCgSliceBytes);
+    attr_set[sizeof(T) == 4] = true;
+  }
+  k_cg_L<T><<<grid, kCgThreads, sm, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, P, Tv, st.done);
   if (ev) cudaEventRecord(ev[1], s);
-  k_cg_LT<T><<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, is_anchor, Tv, P,
+  k_cg_LT<T><<<grid, kCgThreads, sm, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, is_anchor, Tv, P,
                                           Q, st.done, st.partials);
   if (ev) cudaEventRecord(ev[2], s);
   k_cg_alpha<<<cgrid, 256, 0, s>>>(g, st.partials, st.rz, st.alpha, st.done, st.active);

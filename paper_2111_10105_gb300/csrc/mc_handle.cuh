@@ -26,6 +26,7 @@ struct mesh_codec {
   mc::CgState cg;
   uint32_t* d_status;
   int nnz;
+  int max_degree = 0;
   size_t partial_elems;
   // host side
   uint32_t* h_status = nullptr;     // pinned

@@ -174,8 +174,10 @@ struct CgState {
 };
 struct CgGeom {
   int n, W, row_blocks, rows_per_block;
+  int slice_ints;   // shared-memory CSR slice per CTA (ints), 0 = read CSR from global
 };
-CgGeom cg_geometry(int n, int W);
+constexpr int kCgSliceBytes = 96 * 1024;
+CgGeom cg_geometry(int n, int W, int max_degree);
 size_t cg_partials_elems(int n, int W);
 // vectors X, R, P, T, Q are double (single = 0) or float (single = 1) [n][W]
 // inv_d, inv_diag: double (single = 0) or float (single = 1) [n]
