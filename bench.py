@@ -409,6 +409,99 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """64 independent sequences of uneven sizes per step (log-uniform n in
+    [1k, 50k], F ~ U[32, 300], k ~ U[8, min(48, F)], 1% anchors), encoded and
+    decoded through mesh_codec_encode_batch / mesh_codec_decode_batch, each
+    sequence on its own stream."""
+    import torch
+
+    from oracle import metrics
+    from paper_2111_10105_gb300 import MeshCodec
+    from paper_2111_10105_gb300.codec import encode_batch, decode_batch
+    from synth import make_sequence
+    from synth.motion import batched_specs
+
+    world, rank, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    specs = batched_specs(64, seed=1003 + 100 * rank)
+    prec = PRECISION_CODE[args.precision]
+    single = prec != 0
+    codecs, pos_d, pos_h = [], [], []
+    for spec in specs:
+        tris, pos = make_sequence(spec)
+        codecs.append(MeshCodec(tris, pos.shape[1], n_frames=spec.n_frames, rank=spec.rank,
+                                n_anchors=spec.n_anchors, seed=spec.seed, oi_sweeps=SWEEPS,
+                                precision=prec, oi_refine_sweeps=1 if single else 0,
+                                cg_rtol=1e-6 if single else 1e-14, solve_mode=2,
+                                autotune=1 if single else 0))
+        pos_d.append(torch.from_numpy(pos).to(dev))
+        pos_h.append(pos)
+    outs = [torch.empty(c.stream_bytes, dtype=torch.uint8, device=dev) for c in codecs]
+    recs = [torch.empty_like(p) for p in pos_d]
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        bits = encode_batch(codecs, pos_d, outs=outs, stream=stream)
+        decode_batch(codecs, bits, outs=recs, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    sampler = ClockSampler()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    total_ms, launches = 0.0, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        for c in codecs:
+            st = c.stats()
+            launches += st["launches_encode"] + st["launches_decode"]
+    clocks = sampler.stop()
+    vf = sum(p.shape[0] * p.shape[1] for p in pos_h)
+    value, seconds = aggregate(vf * args.steps, total_ms / 1e3, world, dist)
+    nm = [metrics.nmse(p, r.cpu().numpy()) for p, r in zip(pos_h, recs)]
+    iters = [c.stats()["cg_iters_max"] for c in codecs]
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": seconds * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "tf32+f32 (FP64 QR, refinement, quantizer)" if single else "f64",
+            "data": "synthetic",
+            "config": {"workload": "batched64", "sequences": len(specs), "vertex_frames": vf,
+                       "n_range": [min(p.shape[1] for p in pos_h), max(p.shape[1] for p in pos_h)],
+                       "F_range": [min(p.shape[0] for p in pos_h), max(p.shape[0] for p in pos_h)],
+                       "precision": args.precision, "autotune": bool(single),
+                       "l2": "flushed (256 MiB write) before every step",
+                       "parallelism": f"replicas x{world}, one stream per sequence"},
+            "nmse_median": float(statistics.median(nm)), "nmse_max": float(max(nm)),
+            "cg_iters_max": max(iters), "clocks": clocks, "gpu_launches": launches,
+        }
+        print(json.dumps(out), flush=True)
+    for c in codecs:
+        c.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -426,6 +519,8 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched64":
+        return run_batched(args)
     return run_ours(args)
 
 

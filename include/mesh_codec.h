@@ -93,7 +93,10 @@ typedef struct mesh_codec_params {
     uint64_t seed;               /* anchors and the starting basis (splitmix64) */
     int32_t solve_mode;          /* mesh_codec_solve_mode_t */
     int32_t oi_refine_sweeps;    /* mixed precision: FP64 sweeps after the tensor-core ones */
-    int32_t reserved[6];         /* must be zero */
+    int32_t autotune;            /* 1: time candidate CG tile shapes on the first decode of each
+                                    column count and keep the fastest (results then depend on
+                                    the chosen shape at rounding level); 0: fixed shape */
+    int32_t reserved[5];         /* must be zero */
 } mesh_codec_params_t;
 
 typedef struct mesh_codec_stats {
@@ -183,6 +186,30 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_encode_host(mesh_codec_t* h, const
 MESH_CODEC_API mesh_codec_status_t mesh_codec_decode_host(mesh_codec_t* h, const uint8_t* bitstream_host,
                                            size_t bytes, double* positions_out_host,
                                            void* stream);
+
+/* Batches of independent sequences (each with its own handle, connectivity
+ * and sizes).  The work of handle i runs on a stream of its own, forked from
+ * and joined back to `stream` with events, so that sequences of uneven size
+ * overlap on the GPU; the decoders' CG solves advance in lockstep chunks of
+ * 32 iterations.  Arrays have `count` entries; a handle may appear once.
+ * `written[i]` / `statuses[i]` (statuses may be NULL) receive the per-
+ * sequence results; the return value is the first non-OK status.
+ * Synchronises every handle's stream before returning. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_encode_batch(mesh_codec_t* const* handles,
+                                                           int count,
+                                                           const double* const* positions,
+                                                           uint8_t* const* bitstreams,
+                                                           const size_t* capacities,
+                                                           size_t* written,
+                                                           mesh_codec_status_t* statuses,
+                                                           void* stream);
+MESH_CODEC_API mesh_codec_status_t mesh_codec_decode_batch(mesh_codec_t* const* handles,
+                                                           int count,
+                                                           const uint8_t* const* bitstreams,
+                                                           const size_t* bytes,
+                                                           double* const* positions_out,
+                                                           mesh_codec_status_t* statuses,
+                                                           void* stream);
 
 /* Statistics of the last create / encode / decode (synchronises the handle's
  * last stream). */

@@ -42,7 +42,8 @@ class Params(ctypes.Structure):
         ("oi_sweeps", ctypes.c_int32), ("cg_max_iters", ctypes.c_int32),
         ("oi_tol", ctypes.c_double), ("cg_rtol", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("solve_mode", ctypes.c_int32),
-        ("oi_refine_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6),
+        ("oi_refine_sweeps", ctypes.c_int32), ("autotune", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
     ]
 
 
@@ -104,6 +105,8 @@ _SIGS = {
     "mesh_codec_destroy": (None, [_P]),
     "mesh_codec_selftest_gemm": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
+    "mesh_codec_encode_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P]),
+    "mesh_codec_decode_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P]),
     "mesh_codec_adjacency_static": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P,
                                                    ctypes.c_size_t, _P,
                                                    ctypes.POINTER(ctypes.c_int32), _P]),
@@ -331,3 +334,53 @@ def selftest_gemm(kind, A, B, splits=1, stream=None):
                                         ctypes.c_void_p(C.data_ptr()), _stream_ptr(stream)),
            "mesh_codec_selftest_gemm")
     return C
+
+
+def _ptr_array(ptrs, ctype=ctypes.c_void_p):
+    arr = (ctype * len(ptrs))()
+    for i, p in enumerate(ptrs):
+        arr[i] = p
+    return arr
+
+
+def encode_batch(codecs, positions, outs=None, stream=None):
+    """Encode several sequences at once (mesh_codec_encode_batch): one codec
+    per sequence, positions CUDA float64 [F_i, n_i, 3].  Returns the list of
+    bitstreams (CUDA uint8 views)."""
+    torch = _torch()
+    lib = load_library()
+    count = len(codecs)
+    if outs is None:
+        outs = [torch.empty(c.stream_bytes, dtype=torch.uint8, device="cuda") for c in codecs]
+    hs = _ptr_array([c._h.value for c in codecs])
+    ps = _ptr_array([p.data_ptr() for p in positions])
+    bs = _ptr_array([o.data_ptr() for o in outs])
+    caps = _ptr_array([o.numel() for o in outs], ctypes.c_size_t)
+    written = (ctypes.c_size_t * count)()
+    sts = (ctypes.c_int * count)()
+    st = lib.mesh_codec_encode_batch(ctypes.cast(hs, _P), count, ctypes.cast(ps, _P),
+                                     ctypes.cast(bs, _P), ctypes.cast(caps, _P),
+                                     ctypes.cast(written, _P), ctypes.cast(sts, _P),
+                                     _stream_ptr(stream))
+    _check(st, "mesh_codec_encode_batch")
+    return [o[: written[i]] for i, o in enumerate(outs)]
+
+
+def decode_batch(codecs, bitstreams, outs=None, stream=None, allow_not_converged=False):
+    """Decode several sequences at once (mesh_codec_decode_batch)."""
+    torch = _torch()
+    lib = load_library()
+    count = len(codecs)
+    if outs is None:
+        outs = [torch.empty((c.F, c.n, 3), dtype=torch.float64, device="cuda") for c in codecs]
+    hs = _ptr_array([c._h.value for c in codecs])
+    bs = _ptr_array([b.data_ptr() for b in bitstreams])
+    nb = _ptr_array([b.numel() for b in bitstreams], ctypes.c_size_t)
+    os_ = _ptr_array([o.data_ptr() for o in outs])
+    sts = (ctypes.c_int * count)()
+    st = lib.mesh_codec_decode_batch(ctypes.cast(hs, _P), count, ctypes.cast(bs, _P),
+                                     ctypes.cast(nb, _P), ctypes.cast(os_, _P),
+                                     ctypes.cast(sts, _P), _stream_ptr(stream))
+    if not (allow_not_converged and st == 6):
+        _check(st, "mesh_codec_decode_batch")
+    return outs

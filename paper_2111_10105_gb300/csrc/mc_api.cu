@@ -148,7 +148,8 @@ bool valid_params(const mesh_codec_params_t* p) {
   // 3F columns x n rows must be indexable, and the per-coordinate product fit
   if ((long long)p->n_frames * 3 > (1LL << 30)) return false;
   if ((long long)p->n_vertices * 3 * p->n_frames > (1LL << 40)) return false;
-  for (int i = 0; i < 6; ++i)
+  if (p->autotune != 0 && p->autotune != 1) return false;
+  for (int i = 0; i < 5; ++i)
     if (p->reserved[i] != 0) return false;
   return true;
 }
@@ -201,6 +202,10 @@ void mesh_codec_destroy(mesh_codec_t* h) {
   if (h->h_header) cudaFreeHost(h->h_header);
   if (h->h_chg) cudaFreeHost(h->h_chg);
   for (cudaEvent_t e : h->prof_events) cudaEventDestroy(e);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_done) cudaEventDestroy(h->ev_done);
+  if (h->ev_chunk) cudaEventDestroy(h->ev_chunk);
+  if (h->own) cudaStreamDestroy(h->own);
   delete h;
 }
 
@@ -211,7 +216,7 @@ static mesh_codec_status_t create_impl(mesh_codec* h, const int32_t* tris_in, in
   const int n = h->n, T = h->T;
   h->lay = make_layout(n, h->F, h->k, h->n_c, h->p.coeff_bits, h->p.dict_bits,
                        h->p.anchor_bits, h->kind);
-  h->geom = cg_geometry(n, h->W, 0);
+  h->geom = cg_geometry(n, h->W);
   // split-K partial buffer: the largest of the encoder's reductions
   {
     size_t F = h->F, k = h->k;
@@ -230,6 +235,10 @@ static mesh_codec_status_t create_impl(mesh_codec* h, const int32_t* tris_in, in
   MC_TRY(cudaMallocHost(&h->h_active, sizeof(int32_t) * 4));
   MC_TRY(cudaMallocHost(&h->h_header, 64));
   MC_TRY(cudaMallocHost(&h->h_chg, sizeof(double) * 4));
+  MC_TRY(cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking));
+  MC_TRY(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  MC_TRY(cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming));
+  MC_TRY(cudaEventCreateWithFlags(&h->ev_chunk, cudaEventDisableTiming));
   MC_TRY(cudaMemsetAsync(h->d_status, 0, sizeof(uint32_t) * 4, s));
 
   // temporaries for the CSR build
@@ -475,9 +484,14 @@ static bool use_factored(const mesh_codec* h) {
   return false;
 }
 
-static mesh_codec_status_t enqueue_decode(mesh_codec* h, const uint8_t* in, double* out,
-                                          cudaStream_t s, Launches& L) {
+__global__ void k_flag_not_converged(const int32_t* done, int W, uint32_t* status);
+
+// Decoder, in three phases so that several handles can advance their CG
+// solves in lockstep on their own streams (mesh_codec_decode_batch).
+// Phase 1: unpack, back-projection, right-hand sides, CG start.
+static void decode_prepare(mesh_codec* h, const uint8_t* in, cudaStream_t s, Launches& L) {
   const int n = h->n, F = h->F, k = h->k, W = h->W;
+  DecodeState& d = h->dec;
   cudaMemsetAsync(h->d_status, 0, sizeof(uint32_t), s);
   unpack_sections(in, h->lay, h->Udeq, h->Cdeq, h->Ahat, h->dec_anchors, nullptr, h->d_status, s,
                   L);
@@ -486,11 +500,10 @@ static mesh_codec_status_t enqueue_decode(mesh_codec* h, const uint8_t* in, doub
   mark_anchors(h->dec_anchors, h->n_c, h->is_anchor, s, L);
   vertex_scalars_marked(h->row_ptr, h->col_idx, h->deg, h->is_anchor, n, h->kind, h->inv_d,
                         h->inv_diag, s, L);
-  const bool factored = use_factored(h);
+  d.factored = use_factored(h);
   // CG columns: 3F frames (Eq. 11-12 as written), or 3k + n_c factored columns
-  const int Wc = factored ? 3 * k + h->n_c : W;
-  const CgGeom geom = cg_geometry(n, Wc, h->max_degree);
-  if (!factored) {
+  d.Wc = d.factored ? 3 * k + h->n_c : W;
+  if (!d.factored) {
     // delta~_c = (U_c' C_c')^T : (n x k)(k x F) into D[:, cF : cF + F]
     if (h->lp >= 0) {
       mixed_backproject(h, s, L);
@@ -507,53 +520,86 @@ static mesh_codec_status_t enqueue_decode(mesh_codec* h, const uint8_t* in, doub
   } else {
     // E = [C_x'^T | C_y'^T | C_z'^T | 0] (n x Wc); B = L^T E, then column 3k + a of B
     // gets e_{anchor a}:  M Y = L^T C'^T and M G = P^T
-    factored_rhs(h->Cdeq, k, n, Wc, h->D, s, L);
-    laplacian_t_rows(h->row_ptr, h->col_idx, h->deg, h->inv_d, h->D, h->B, n, Wc, h->kind, s, L);
-    unit_anchor_columns(h->B, h->dec_anchors, h->n_c, Wc, 3 * k, s, L);
+    factored_rhs(h->Cdeq, k, n, d.Wc, h->D, s, L);
+    laplacian_t_rows(h->row_ptr, h->col_idx, h->deg, h->inv_d, h->D, h->B, n, d.Wc, h->kind, s,
+                     L);
+    unit_anchor_columns(h->B, h->dec_anchors, h->n_c, d.Wc, 3 * k, s, L);
   }
-  // CG: FP64 vectors, or FP32 vectors with FP64 dot products in the mixed modes
-  const int single = h->lp >= 0 ? 1 : 0;
-  const void* inv_d = h->inv_d;
-  const void* inv_diag = h->inv_diag;
-  if (single) {   // FP32 copies: no FP64 conversions in the FP32 kernels
+  // CG: FP64 vectors, or FP32 vectors with FP64-accurate dot products in the mixed modes
+  d.single = h->lp >= 0 ? 1 : 0;
+  d.inv_d = h->inv_d;
+  d.inv_diag = h->inv_diag;
+  if (d.single) {   // FP32 copies: no FP64 conversions in the FP32 kernels
     narrow(h->inv_d, n, h->inv_d32, s, L);
     narrow(h->inv_diag, n, h->inv_diag32, s, L);
-    inv_d = h->inv_d32;
-    inv_diag = h->inv_diag32;
+    d.inv_d = h->inv_d32;
+    d.inv_diag = h->inv_diag32;
   }
-  cg_init(geom, h->B, h->X, h->R, h->P, inv_diag, h->cg, single, s, L);
-  h->cg_columns = Wc;
-  const int batch = 32;
-  int it = 0;
-  while (it < h->p.cg_max_iters) {
-    int m = std::min(batch, h->p.cg_max_iters - it);
-    for (int j = 0; j < m; ++j)
-      cg_iteration(geom, h->row_ptr, h->col_idx, h->deg, inv_d, h->is_anchor, inv_diag, h->kind,
-                   h->X, h->R, h->P, h->Tv, h->Qv, h->p.cg_rtol, h->p.cg_max_iters, h->cg, single,
-                   s, L, prof_group(h, it + j));
-    it += m;
-    MC_TRY(cudaMemcpyAsync(h->h_active, h->cg.active, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  d.geom = cg_geometry(n, d.Wc);
+  if (h->p.autotune) {
+    if (h->tuned_W != d.Wc || h->tuned_single != d.single) {
+      h->tuned = cg_autotune(n, d.Wc, h->row_ptr, h->col_idx, h->deg, d.inv_d, h->is_anchor,
+                             h->kind, h->P, h->Tv, h->Qv, h->cg, d.single, s, L);
+      h->tuned_W = d.Wc;
+      h->tuned_single = d.single;
+    }
+    d.geom = h->tuned;
+  }
+  cg_init(d.geom, h->B, h->X, h->R, h->P, d.inv_diag, h->cg, d.single, s, L);
+  h->cg_columns = d.Wc;
+  d.it = 0;
+}
+
+// Phase 2: up to `m` CG iterations, then an asynchronous copy of the number
+// of still active columns to pinned host memory.  Returns false when the
+// iteration cap has been reached.
+static bool decode_cg_chunk(mesh_codec* h, int m, cudaStream_t s, Launches& L) {
+  DecodeState& d = h->dec;
+  m = std::min(m, h->p.cg_max_iters - d.it);
+  if (m <= 0) return false;
+  for (int j = 0; j < m; ++j)
+    cg_iteration(d.geom, h->row_ptr, h->col_idx, h->deg, d.inv_d, h->is_anchor, d.inv_diag,
+                 h->kind, h->X, h->R, h->P, h->Tv, h->Qv, h->p.cg_rtol, h->p.cg_max_iters, h->cg,
+                 d.single, s, L, prof_group(h, d.it + j));
+  d.it += m;
+  cudaMemcpyAsync(h->h_active, h->cg.active, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  return true;
+}
+
+// Phase 3: the solution in FP64, the factored combination, the output layout.
+static void decode_finish(mesh_codec* h, double* out, cudaStream_t s, Launches& L) {
+  const int n = h->n, F = h->F, k = h->k, W = h->W;
+  const DecodeState& d = h->dec;
+  const double* Xs = h->X;
+  if (d.single) {   // the mixed modes widen their FP32 iterate into B
+    widen((const float*)h->X, (long long)n * d.Wc, h->B, s, L);
+    Xs = h->B;
+  }
+  if (!d.factored) {
+    vertex_major_to_frames(Xs, out, F, n, s, L);
+  } else {
+    // X_c = Y_c U_c'^T + G A^_c into D [n][3F]
+    dgemm(n, F, k, 3, Strided{Xs, d.Wc, 1, k}, Strided{h->Udeq, 1, k, (long long)F * k},
+          StridedOut{h->D, W, 1, F}, 1, nullptr, s, L);
+    StridedOut acc{h->D, W, 1, F};
+    acc.accumulate = 1;
+    dgemm(n, F, h->n_c, 3, Strided{Xs + 3 * k, d.Wc, 1, 0},
+          Strided{h->Ahat, F, 1, (long long)std::max(h->n_c, 1) * F}, acc, 1, nullptr, s, L);
+    vertex_major_to_frames(h->D, out, F, n, s, L);
+  }
+  k_flag_not_converged<<<(h->cg_columns + 255) / 256, 256, 0, s>>>(h->cg.done, h->cg_columns,
+                                                                     h->d_status);
+  L.add(1);
+}
+
+static mesh_codec_status_t enqueue_decode(mesh_codec* h, const uint8_t* in, double* out,
+                                          cudaStream_t s, Launches& L) {
+  decode_prepare(h, in, s, L);
+  while (decode_cg_chunk(h, 32, s, L)) {
     MC_TRY(cudaStreamSynchronize(s));
     if (*h->h_active == 0) break;
   }
-  // the solution as FP64 (the mixed modes widen their FP32 iterate into B)
-  const double* Xs = h->X;
-  if (single) {
-    widen((const float*)h->X, (long long)n * Wc, h->B, s, L);
-    Xs = h->B;
-  }
-  if (!factored) {
-    vertex_major_to_frames(Xs, out, F, n, s, L);
-    return MC_OK;
-  }
-  // X_c = Y_c U_c'^T + G A^_c into D [n][3F]
-  dgemm(n, F, k, 3, Strided{Xs, Wc, 1, k}, Strided{h->Udeq, 1, k, (long long)F * k},
-        StridedOut{h->D, W, 1, F}, 1, nullptr, s, L);
-  StridedOut acc{h->D, W, 1, F};
-  acc.accumulate = 1;
-  dgemm(n, F, h->n_c, 3, Strided{Xs + 3 * k, Wc, 1, 0},
-        Strided{h->Ahat, F, 1, (long long)std::max(h->n_c, 1) * F}, acc, 1, nullptr, s, L);
-  vertex_major_to_frames(h->D, out, F, n, s, L);
+  decode_finish(h, out, s, L);
   return MC_OK;
 }
 
@@ -578,9 +624,6 @@ mesh_codec_status_t mesh_codec_decode(mesh_codec_t* h, const uint8_t* bitstream,
   Launches L{&h->launches_decode};
   st = enqueue_decode(h, bitstream, positions_out, s, L);
   if (st != MC_OK) return st;
-  k_flag_not_converged<<<(h->cg_columns + 255) / 256, 256, 0, s>>>(h->cg.done, h->cg_columns,
-                                                                     h->d_status);
-  L.add(1);
   MC_TRY(cudaGetLastError());
   st = read_status(h, s);
   prof_collect(h);
@@ -630,15 +673,141 @@ mesh_codec_status_t mesh_codec_decode_host(mesh_codec_t* h, const uint8_t* bitst
   Launches L{&h->launches_decode};
   st = enqueue_decode(h, h->stage_bits, h->stage_pos, s, L);
   if (st != MC_OK) return st;
-  k_flag_not_converged<<<(h->cg_columns + 255) / 256, 256, 0, s>>>(h->cg.done, h->cg_columns,
-                                                                     h->d_status);
-  L.add(1);
   MC_TRY(cudaMemcpyAsync(positions_out_host, h->stage_pos, sizeof(double) * 3ull * h->n * h->F,
                          cudaMemcpyDeviceToHost, s));
   MC_TRY(cudaGetLastError());
   st = read_status(h, s);
   prof_collect(h);
   return st;
+}
+
+// ------------------------------------------------------------ batches
+// Each handle runs on its own stream, forked from and joined back to the
+// caller's stream with events, so independent sequences of uneven sizes
+// overlap on the GPU.
+static bool batch_args_ok(mesh_codec_t* const* hs, int count) {
+  if (!hs || count < 1) return false;
+  for (int i = 0; i < count; ++i)
+    if (!hs[i]) return false;
+  for (int i = 0; i < count; ++i)
+    for (int j = i + 1; j < count; ++j)
+      if (hs[i] == hs[j]) return false;   // a handle's workspace is used once per batch
+  return true;
+}
+
+mesh_codec_status_t mesh_codec_encode_batch(mesh_codec_t* const* handles, int count,
+                                            const double* const* positions,
+                                            uint8_t* const* bitstreams,
+                                            const size_t* capacities, size_t* written,
+                                            mesh_codec_status_t* statuses, void* stream) {
+  if (!batch_args_ok(handles, count) || !positions || !bitstreams || !capacities || !written)
+    return MC_E_INVALID_ARG;
+  cudaStream_t s0 = (cudaStream_t)stream;
+  MC_TRY(cudaEventRecord(handles[0]->ev_fork, s0));
+  std::vector<mesh_codec_status_t> st(count, MC_OK);
+  for (int i = 0; i < count; ++i) {
+    mesh_codec* h = handles[i];
+    written[i] = (size_t)h->lay.total;
+    if (!positions[i] || !bitstreams[i] || ((uintptr_t)bitstreams[i] & 7)) {
+      st[i] = MC_E_INVALID_ARG;
+      continue;
+    }
+    if (capacities[i] < (size_t)h->lay.total) {
+      st[i] = MC_E_BUFFER_TOO_SMALL;
+      continue;
+    }
+    MC_TRY(cudaStreamWaitEvent(h->own, handles[0]->ev_fork, 0));
+    h->last_stream = h->own;
+    h->launches_encode = 0;
+    Launches L{&h->launches_encode};
+    enqueue_encode(h, positions[i], bitstreams[i], h->own, L, false);
+    MC_TRY(cudaEventRecord(h->ev_done, h->own));
+    MC_TRY(cudaStreamWaitEvent(s0, h->ev_done, 0));
+  }
+  mesh_codec_status_t first = MC_OK;
+  for (int i = 0; i < count; ++i) {
+    if (st[i] == MC_OK) st[i] = read_status(handles[i], handles[i]->own);
+    if (statuses) statuses[i] = st[i];
+    if (first == MC_OK) first = st[i];
+  }
+  return first;
+}
+
+mesh_codec_status_t mesh_codec_decode_batch(mesh_codec_t* const* handles, int count,
+                                            const uint8_t* const* bitstreams,
+                                            const size_t* bytes, double* const* positions_out,
+                                            mesh_codec_status_t* statuses, void* stream) {
+  if (!batch_args_ok(handles, count) || !bitstreams || !bytes || !positions_out)
+    return MC_E_INVALID_ARG;
+  cudaStream_t s0 = (cudaStream_t)stream;
+  MC_TRY(cudaEventRecord(handles[0]->ev_fork, s0));
+  std::vector<mesh_codec_status_t> st(count, MC_OK);
+  // headers, all at once
+  for (int i = 0; i < count; ++i) {
+    mesh_codec* h = handles[i];
+    if (!bitstreams[i] || !positions_out[i] || ((uintptr_t)bitstreams[i] & 7) ||
+        ((uintptr_t)positions_out[i] & 7) || h->n_c == 0) {
+      st[i] = MC_E_INVALID_ARG;
+      continue;
+    }
+    if (bytes[i] < 64) {
+      st[i] = MC_E_BITSTREAM_CORRUPT;
+      continue;
+    }
+    MC_TRY(cudaStreamWaitEvent(h->own, handles[0]->ev_fork, 0));
+    MC_TRY(cudaMemcpyAsync(h->h_header, bitstreams[i], 64, cudaMemcpyDeviceToHost, h->own));
+  }
+  for (int i = 0; i < count; ++i) {
+    if (st[i] != MC_OK) continue;
+    MC_TRY(cudaStreamSynchronize(handles[i]->own));
+    st[i] = check_header(handles[i], handles[i]->h_header, bytes[i]);
+  }
+  // phase 1 for every sequence, then their CG solves in lockstep chunks
+  std::vector<int> active;
+  for (int i = 0; i < count; ++i) {
+    if (st[i] != MC_OK) continue;
+    mesh_codec* h = handles[i];
+    h->last_stream = h->own;
+    h->launches_decode = 0;
+    Launches L{&h->launches_decode};
+    decode_prepare(h, bitstreams[i], h->own, L);
+    active.push_back(i);
+  }
+  while (!active.empty()) {
+    std::vector<int> issued;
+    for (int i : active) {
+      mesh_codec* h = handles[i];
+      Launches L{&h->launches_decode};
+      if (decode_cg_chunk(h, 32, h->own, L)) {
+        MC_TRY(cudaEventRecord(h->ev_chunk, h->own));
+        issued.push_back(i);
+      }
+    }
+    std::vector<int> still;
+    for (int i : issued) {
+      MC_TRY(cudaEventSynchronize(handles[i]->ev_chunk));
+      if (*handles[i]->h_active != 0) still.push_back(i);
+    }
+    active.swap(still);
+  }
+  for (int i = 0; i < count; ++i) {
+    if (st[i] != MC_OK) continue;
+    mesh_codec* h = handles[i];
+    Launches L{&h->launches_decode};
+    decode_finish(h, positions_out[i], h->own, L);
+    MC_TRY(cudaEventRecord(h->ev_done, h->own));
+    MC_TRY(cudaStreamWaitEvent(s0, h->ev_done, 0));
+  }
+  mesh_codec_status_t first = MC_OK;
+  for (int i = 0; i < count; ++i) {
+    if (st[i] == MC_OK) {
+      st[i] = read_status(handles[i], handles[i]->own);
+      prof_collect(handles[i]);
+    }
+    if (statuses) statuses[i] = st[i];
+    if (first == MC_OK) first = st[i];
+  }
+  return first;
 }
 
 mesh_codec_status_t mesh_codec_set_profiling(mesh_codec_t* h, int every) {

@@ -26,25 +26,30 @@ namespace mc {
 
 static constexpr int kCgThreads = 256;  // 32 columns x 8 row lanes
 
-CgGeom cg_geometry(int n, int W, int max_degree) {
+CgGeom cg_geometry_rows(int n, int W, int rpb) {
   CgGeom g{};
   g.n = n;
   g.W = W;
-  int col_tiles = (W + 31) / 32;
-  long long target = std::max(1, (152 * 16) / std::max(1, col_tiles));
-  int rpb = (int)((n + target - 1) / target);
   rpb = std::max(8, (rpb + 7) / 8 * 8);
   g.rows_per_block = rpb;
   g.row_blocks = (n + rpb - 1) / rpb;
-  // shared-memory CSR slice: row offsets + at most rows * max_degree indices
-  long long ints = (long long)rpb + 1 + (long long)rpb * std::max(max_degree, 0);
-  g.slice_ints = (max_degree > 0 && ints * 4 <= kCgSliceBytes) ? (int)ints : 0;
   return g;
 }
 
+// default shape: about 16 CTAs of 32 columns x 8 row lanes per SM
+CgGeom cg_geometry(int n, int W) {
+  int col_tiles = (W + 31) / 32;
+  long long target = std::max(1, (152 * 16) / std::max(1, col_tiles));
+  return cg_geometry_rows(n, W, (int)((n + target - 1) / target));
+}
+
+// the autotuner's candidates: the default rows per CTA times 1/2, 1, 2, 4
+static const int kTuneNum[4] = {1, 1, 2, 4}, kTuneDen[4] = {2, 1, 1, 1};
+
 size_t cg_partials_elems(int n, int W) {
-  CgGeom g = cg_geometry(n, W, 0);
-  return (size_t)g.row_blocks * W * 2;
+  const CgGeom g = cg_geometry(n, W);
+  const CgGeom h = cg_geometry_rows(n, W, g.rows_per_block / 2);   // most row blocks
+  return (size_t)std::max(g.row_blocks, h.row_blocks) * W * 2;
 }
 
 // Combine the 8 row-lane partial sums of a column in fixed order and store
@@ -148,30 +153,12 @@ __global__ void k_cg_init_cols(CgGeom g, const double* __restrict__ partials, do
   }
 }
 
-// The CSR slice of a CTA's row block (relative row offsets, then column
-// indices) is staged in shared memory once per launch when it fits
-// (g.slice_ints > 0): every row then costs one dependent global load (the
-// neighbours' values) instead of three.  Neighbour values are loaded four at
-// a time and summed in ascending order, the same order as one at a time.
+// Neighbour values are loaded four at a time (independent loads in flight)
+// and summed in ascending column order, the same order as one at a time.
 struct CsrView {
   const int32_t* rp;   // row offsets, indexed by row - r0
-  const int32_t* ci;   // column indices, indexed by the offsets in rp
+  const int32_t* ci;   // column indices
 };
-
-__device__ __forceinline__ CsrView stage_csr(const CgGeom& g, const int32_t* __restrict__ row_ptr,
-                                             const int32_t* __restrict__ col_idx, long long r0,
-                                             long long r1, int32_t* smem) {
-  if (g.slice_ints <= 0) return CsrView{row_ptr + r0, col_idx};
-  const int nrows = (int)(r1 - r0);
-  const int base = row_ptr[r0];
-  const int nnz_s = row_ptr[r1] - base;
-  int32_t* s_rp = smem;
-  int32_t* s_ci = smem + g.rows_per_block + 1;
-  for (int t = threadIdx.x; t <= nrows; t += blockDim.x) s_rp[t] = row_ptr[r0 + t] - base;
-  for (int t = threadIdx.x; t < nnz_s; t += blockDim.x) s_ci[t] = col_idx[base + t];
-  __syncthreads();
-  return CsrView{s_rp, s_ci};
-}
 
 // sum over p in [b, e) of V[ci[p]*W + col], ascending p
 template <typename T>
@@ -223,12 +210,11 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_L(CgGeom g, const int32_t* __
                                                      const T* __restrict__ inv_d, int kind,
                                                      const T* __restrict__ P, T* __restrict__ Tv,
                                                      const int32_t* __restrict__ done) {
-  extern __shared__ int32_t s_csr[];
   const int col = blockIdx.x * 32 + (threadIdx.x & 31);
   const int rl = threadIdx.x >> 5;
   const long long r0 = (long long)blockIdx.y * g.rows_per_block;
   const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
-  const CsrView v = stage_csr(g, row_ptr, col_idx, r0, r1, s_csr);
+  const CsrView v{row_ptr + r0, col_idx};
   if (col >= g.W || done[col]) return;
   for (long long i = r0 + rl; i < r1; i += 8) {
     const int b = v.rp[i - r0], e = v.rp[i - r0 + 1];
@@ -249,13 +235,12 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_LT(CgGeom g, const int32_t* _
                                                       const T* __restrict__ P, T* __restrict__ Q,
                                                       const int32_t* __restrict__ done,
                                                       double* __restrict__ partials) {
-  extern __shared__ int32_t s_csr[];
   __shared__ double sh[256];
   const int col = blockIdx.x * 32 + (threadIdx.x & 31);
   const int rl = threadIdx.x >> 5;
   const long long r0 = (long long)blockIdx.y * g.rows_per_block;
   const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
-  const CsrView v = stage_csr(g, row_ptr, col_idx, r0, r1, s_csr);
+  const CsrView v{row_ptr + r0, col_idx};
   const bool valid = col < g.W && !done[col];
   DotAcc<T> pap;
   if (valid) {
@@ -395,16 +380,9 @@ static void cg_iteration_t(const CgGeom& g, const int32_t* row_ptr, const int32_
   dim3 grid((g.W + 31) / 32, g.row_blocks);
   dim3 cgrid((g.W + 7) / 8);
   if (ev) cudaEventRecord(ev[0], s);
-  const size_t sm = g.slice_ints > 0 ? sizeof(int32_t) * (size_t)g.slice_ints : 0;
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[sizeof(T) == 4]) {
-    cudaFuncSetAttribute(k_cg_L<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCgSliceBytes);
-    cudaFuncSetAttribute(k_cg_LT<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCgSliceBytes);
-    attr_set[sizeof(T) == 4] = true;
-  }
-  k_cg_L<T><<<grid, kCgThreads, sm, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, P, Tv, st.done);
+  k_cg_L<T><<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, P, Tv, st.done);
   if (ev) cudaEventRecord(ev[1], s);
-  k_cg_LT<T><<<grid, kCgThreads, sm, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, is_anchor, Tv, P,
+  k_cg_LT<T><<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, is_anchor, Tv, P,
                                           Q, st.done, st.partials);
   if (ev) cudaEventRecord(ev[2], s);
   k_cg_alpha<<<cgrid, 256, 0, s>>>(g, st.partials, st.rz, st.alpha, st.done, st.active);
@@ -435,6 +413,63 @@ void cg_iteration(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_id
                            (const double*)inv_diag, kind,
                            (double*)X, (double*)R, (double*)P, (double*)T, (double*)Q, rtol,
                            max_iters, st, s, L, ev);
+}
+
+// Autotuner of the CG tile shape: times one operator application (k_cg_L +
+// k_cg_LT, the two gather kernels) for each candidate rows-per-CTA on the
+// current vectors and returns the fastest shape.  The other kernels share it.
+CgGeom cg_autotune(int n, int W, const int32_t* row_ptr, const int32_t* col_idx,
+                   const int32_t* deg, const void* inv_d, const uint8_t* is_anchor, int kind,
+                   void* P, void* T, void* Q, CgState& st, int single, cudaStream_t s,
+                   Launches& L) {
+  const CgGeom base = cg_geometry(n, W);
+  CgGeom best = base;
+  float best_ms = 1e30f;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return base;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return base;
+  }
+  cudaMemsetAsync(st.done, 0, sizeof(int32_t) * W, s);
+  cudaMemsetAsync(P, 0, (single ? 4 : 8) * (size_t)n * W, s);
+  for (int c = 0; c < 4; ++c) {
+    const CgGeom g = cg_geometry_rows(n, W, base.rows_per_block * kTuneNum[c] / kTuneDen[c]);
+    dim3 grid((g.W + 31) / 32, g.row_blocks);
+    float ms = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {   // first repetition warms up
+      cudaEventRecord(e0, s);
+      if (single) {
+        k_cg_L<float><<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, (const float*)inv_d,
+                                                  kind, (const float*)P, (float*)T, st.done);
+        k_cg_LT<float><<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, (const float*)inv_d,
+                                                   kind, is_anchor, (const float*)T,
+                                                   (const float*)P, (float*)Q, st.done,
+                                                   st.partials);
+      } else {
+        k_cg_L<double><<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg,
+                                                   (const double*)inv_d, kind, (const double*)P,
+                                                   (double*)T, st.done);
+        k_cg_LT<double><<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg,
+                                                    (const double*)inv_d, kind, is_anchor,
+                                                    (const double*)T, (const double*)P,
+                                                    (double*)Q, st.done, st.partials);
+      }
+      cudaEventRecord(e1, s);
+      L.add(2);
+      cudaEventSynchronize(e1);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (rep > 0) ms += t;
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = g;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
 }
 
 // out[e] = (double) X[e]

@@ -6,6 +6,15 @@
 
 #include "mc_internal.cuh"
 
+// per-decode state carried between the decoder's phases
+struct DecodeState {
+  bool factored = false;
+  int Wc = 0, single = 0, it = 0;
+  mc::CgGeom geom{};
+  const void* inv_d = nullptr;
+  const void* inv_diag = nullptr;
+};
+
 struct mesh_codec {
   mesh_codec_params_t p;
   int n, T, F, k, W, n_c, kind;
@@ -58,6 +67,12 @@ struct mesh_codec {
   alignas(64) unsigned char map_X[128], map_Qt[128], map_XT[128], map_Wt[128];
   alignas(64) unsigned char map_D[128], map_Ut[128], map_C[128], map_U[128];
   int refine_sweeps = 0;
+  // decoder phases, CG geometry autotuning, own stream for the batch entry points
+  DecodeState dec;
+  mc::CgGeom tuned{};
+  int tuned_W = -1, tuned_single = -1;
+  cudaStream_t own = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_done = nullptr, ev_chunk = nullptr;
 };
 
 namespace mc {

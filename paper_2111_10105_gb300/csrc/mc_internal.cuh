@@ -174,10 +174,13 @@ struct CgState {
 };
 struct CgGeom {
   int n, W, row_blocks, rows_per_block;
-  int slice_ints;   // shared-memory CSR slice per CTA (ints), 0 = read CSR from global
 };
-constexpr int kCgSliceBytes = 96 * 1024;
-CgGeom cg_geometry(int n, int W, int max_degree);
+CgGeom cg_geometry(int n, int W);
+CgGeom cg_geometry_rows(int n, int W, int rows_per_block);
+CgGeom cg_autotune(int n, int W, const int32_t* row_ptr, const int32_t* col_idx,
+                   const int32_t* deg, const void* inv_d, const uint8_t* is_anchor, int kind,
+                   void* P, void* T, void* Q, CgState& st, int single, cudaStream_t s,
+                   Launches& L);
 size_t cg_partials_elems(int n, int W);
 // vectors X, R, P, T, Q are double (single = 0) or float (single = 1) [n][W]
 // inv_d, inv_diag: double (single = 0) or float (single = 1) [n]
