@@ -206,6 +206,8 @@ void mesh_codec_destroy(mesh_codec_t* h) {
   if (h->ev_done) cudaEventDestroy(h->ev_done);
   if (h->ev_chunk) cudaEventDestroy(h->ev_chunk);
   if (h->own) cudaStreamDestroy(h->own);
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->cap) cudaStreamDestroy(h->cap);
   delete h;
 }
 
@@ -236,6 +238,7 @@ static mesh_codec_status_t create_impl(mesh_codec* h, const int32_t* tris_in, in
   MC_TRY(cudaMallocHost(&h->h_header, 64));
   MC_TRY(cudaMallocHost(&h->h_chg, sizeof(double) * 4));
   MC_TRY(cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking));
+  MC_TRY(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
   MC_TRY(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   MC_TRY(cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming));
   MC_TRY(cudaEventCreateWithFlags(&h->ev_chunk, cudaEventDisableTiming));
@@ -553,14 +556,57 @@ static void decode_prepare(mesh_codec* h, const uint8_t* in, cudaStream_t s, Lau
 // Phase 2: up to `m` CG iterations, then an asynchronous copy of the number
 // of still active columns to pinned host memory.  Returns false when the
 // iteration cap has been reached.
+// A full chunk of CG iterations is replayed from a CUDA graph captured once
+// per (column count, precision, tile shape): one launch instead of six per
+// iteration.  Kernel timing (mesh_codec_set_profiling) uses direct launches.
+static constexpr int kCgChunk = 32;
+
+static bool chunk_graph(mesh_codec* h) {
+  const DecodeState& d = h->dec;
+  if (h->graph_exec && h->graph_W == d.Wc && h->graph_single == d.single &&
+      h->graph_rpb == d.geom.rows_per_block)
+    return true;
+  if (h->graph_exec) {
+    cudaGraphExecDestroy(h->graph_exec);
+    h->graph_exec = nullptr;
+  }
+  if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+  Launches none{nullptr};
+  for (int j = 0; j < kCgChunk; ++j)
+    cg_iteration(d.geom, h->row_ptr, h->col_idx, h->deg, d.inv_d, h->is_anchor, d.inv_diag,
+                 h->kind, h->X, h->R, h->P, h->Tv, h->Qv, h->p.cg_rtol, h->p.cg_max_iters, h->cg,
+                 d.single, h->cap, none, nullptr);
+  cudaGraph_t g = nullptr;
+  if (cudaStreamEndCapture(h->cap, &g) != cudaSuccess || !g) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaError_t e = cudaGraphInstantiate(&h->graph_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->graph_exec = nullptr;
+    cudaGetLastError();
+    return false;
+  }
+  h->graph_W = d.Wc;
+  h->graph_single = d.single;
+  h->graph_rpb = d.geom.rows_per_block;
+  return true;
+}
+
 static bool decode_cg_chunk(mesh_codec* h, int m, cudaStream_t s, Launches& L) {
   DecodeState& d = h->dec;
   m = std::min(m, h->p.cg_max_iters - d.it);
   if (m <= 0) return false;
-  for (int j = 0; j < m; ++j)
-    cg_iteration(d.geom, h->row_ptr, h->col_idx, h->deg, d.inv_d, h->is_anchor, d.inv_diag,
-                 h->kind, h->X, h->R, h->P, h->Tv, h->Qv, h->p.cg_rtol, h->p.cg_max_iters, h->cg,
-                 d.single, s, L, prof_group(h, d.it + j));
+  if (m == kCgChunk && h->prof_every == 0 && chunk_graph(h)) {
+    cudaGraphLaunch(h->graph_exec, s);
+    L.add(6 * kCgChunk);
+  } else {
+    for (int j = 0; j < m; ++j)
+      cg_iteration(d.geom, h->row_ptr, h->col_idx, h->deg, d.inv_d, h->is_anchor, d.inv_diag,
+                   h->kind, h->X, h->R, h->P, h->Tv, h->Qv, h->p.cg_rtol, h->p.cg_max_iters,
+                   h->cg, d.single, s, L, prof_group(h, d.it + j));
+  }
   d.it += m;
   cudaMemcpyAsync(h->h_active, h->cg.active, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
   return true;

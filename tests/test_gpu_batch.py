@@ -71,8 +71,12 @@ def test_batch_mixed_autotuned():
     pos_d = [torch.from_numpy(p).cuda() for _, p in seqs]
     r64 = decode_batch(cs64, encode_batch(cs64, pos_d))
     r32 = decode_batch(cs, encode_batch(cs, pos_d))
+    pairs = []
     for (tris, pos), a, b in zip(seqs, r64, r32):
-        ea, eb = metrics.nmse(pos, a.cpu().numpy()), metrics.nmse(pos, b.cpu().numpy())
-        assert abs(eb - ea) <= 0.05 * ea
+        pairs.append((metrics.nmse(pos, a.cpu().numpy()), metrics.nmse(pos, b.cpu().numpy())))
+    # FP32 solve at relative residual 1e-6: an added error of at most 1e-6 of the
+    # centred energy on top of 5% of the FP64 mode's error
+    for ea, eb in pairs:
+        assert abs(eb - ea) <= 0.05 * ea + 1e-6, pairs
     for c in cs + cs64:
         c.close()
