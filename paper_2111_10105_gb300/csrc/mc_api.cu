@@ -40,7 +40,8 @@ struct Carver {
 size_t carve(mesh_codec* h, void* base) {
   Carver c(base);
   const size_t n = h->n, F = h->F, k = h->k, nc = std::max(h->n_c, 1);
-  const size_t W = std::max<size_t>(h->W, 3 * k + h->n_c);   // CG columns, either mode
+  // CG columns, either mode (factored: 3k + n_c, padded to a multiple of 4)
+  const size_t W = std::max<size_t>(h->W, (3 * k + h->n_c + 3) / 4 * 4);
   const size_t nnz_max = 6ull * h->T;
   h->row_ptr = c.take<int32_t>(n + 1);
   h->col_idx = c.take<int32_t>(nnz_max);
@@ -86,7 +87,7 @@ size_t carve(mesh_codec* h, void* base) {
   h->cg.done = c.take<int32_t>(W);
   h->cg.iters = c.take<int32_t>(W);
   h->cg.partials = c.take<double>(std::max(cg_partials_elems(h->n, h->W),
-                                          cg_partials_elems(h->n, 3 * h->k + h->n_c)));
+                                          cg_partials_elems(h->n, (3 * h->k + h->n_c + 3) / 4 * 4)));
   h->cg.active = c.take<int32_t>(1);
   h->cg.all_done = c.take<int32_t>(1);
   h->d_status = c.take<uint32_t>(4);
@@ -505,7 +506,10 @@ static void decode_prepare(mesh_codec* h, const uint8_t* in, cudaStream_t s, Lau
                         h->inv_diag, s, L);
   d.factored = use_factored(h);
   // CG columns: 3F frames (Eq. 11-12 as written), or 3k + n_c factored columns
+  // (the FP32 factored solve pads its column count to a multiple of 4 with
+  // zero right-hand sides, which converge at once, for the float4 kernels)
   d.Wc = d.factored ? 3 * k + h->n_c : W;
+  if (d.factored && h->lp >= 0) d.Wc = (d.Wc + 3) / 4 * 4;
   if (!d.factored) {
     // delta~_c = (U_c' C_c')^T : (n x k)(k x F) into D[:, cF : cF + F]
     if (h->lp >= 0) {

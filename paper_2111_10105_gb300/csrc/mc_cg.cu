@@ -367,8 +367,38 @@ static void cg_init_t(const CgGeom& g, const double* B, void* X, void* R, void* 
 
 void cg_init(const CgGeom& g, const double* B, void* X, void* R, void* P,
              const void* inv_diag, CgState& st, int single, cudaStream_t s, Launches& L) {
-  if (single) cg_init_t<float>(g, B, X, R, P, inv_diag, st, s, L);
-  else cg_init_t<double>(g, B, X, R, P, inv_diag, st, s, L);
+  if (cg4_applies(g.W, single)) {
+    cg4_init(g, B, (float*)X, (float*)R, (float*)P, (const float*)inv_diag, st.partials, s);
+    k_cg_init_cols<<<(g.W + 7) / 8, 256, 0, s>>>(g, st.partials, st.rz, st.bb, st.done,
+                                                 st.iters);
+    L.add(2);
+  } else if (single) {
+    cg_init_t<float>(g, B, X, R, P, inv_diag, st, s, L);
+  } else {
+    cg_init_t<double>(g, B, X, R, P, inv_diag, st, s, L);
+  }
+}
+
+// the four-columns-per-thread FP32 iteration (same kernels for alpha / beta)
+static void cg_iteration4(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx,
+                          const int32_t* deg, const float* inv_d, const uint8_t* is_anchor,
+                          const float* inv_diag, int kind, float* X, float* R, float* P,
+                          float* Tv, float* Q, double rtol, int max_iters, CgState& st,
+                          cudaStream_t s, Launches& L, cudaEvent_t* ev) {
+  dim3 cgrid((g.W + 7) / 8);
+  if (ev) cudaEventRecord(ev[0], s);
+  cg4_op(g, row_ptr, col_idx, deg, inv_d, kind, is_anchor, P, Tv, Q, st.done, st.partials, s, ev);
+  if (ev) cudaEventRecord(ev[2], s);
+  k_cg_alpha<<<cgrid, 256, 0, s>>>(g, st.partials, st.rz, st.alpha, st.done, st.active);
+  if (ev) cudaEventRecord(ev[3], s);
+  cg4_update(g, X, R, P, Q, inv_diag, st.alpha, st.done, st.partials, s);
+  if (ev) cudaEventRecord(ev[4], s);
+  k_cg_beta<<<cgrid, 256, 0, s>>>(g, st.partials, st.rz, st.rr, st.bb, st.beta, st.done,
+                                  st.iters, rtol * rtol, max_iters, st.active);
+  if (ev) cudaEventRecord(ev[5], s);
+  cg4_dir(g, R, P, inv_diag, st.beta, st.done, s);
+  if (ev) cudaEventRecord(ev[6], s);
+  L.add(6);
 }
 
 template <typename T>
@@ -403,7 +433,11 @@ void cg_iteration(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_id
                   const void* inv_diag, int kind, void* X, void* R, void* P, void* T, void* Q,
                   double rtol, int max_iters, CgState& st, int single, cudaStream_t s,
                   Launches& L, cudaEvent_t* ev) {
-  if (single)
+  if (cg4_applies(g.W, single))
+    cg_iteration4(g, row_ptr, col_idx, deg, (const float*)inv_d, is_anchor,
+                  (const float*)inv_diag, kind, (float*)X, (float*)R, (float*)P, (float*)T,
+                  (float*)Q, rtol, max_iters, st, s, L, ev);
+  else if (single)
     cg_iteration_t<float>(g, row_ptr, col_idx, deg, (const float*)inv_d, is_anchor,
                           (const float*)inv_diag, kind, (float*)X,
                           (float*)R, (float*)P, (float*)T, (float*)Q, rtol, max_iters, st, s, L,
@@ -439,7 +473,10 @@ CgGeom cg_autotune(int n, int W, const int32_t* row_ptr, const int32_t* col_idx,
     float ms = 0.f;
     for (int rep = 0; rep < 3; ++rep) {   // first repetition warms up
       cudaEventRecord(e0, s);
-      if (single) {
+      if (cg4_applies(g.W, single)) {
+        cg4_op(g, row_ptr, col_idx, deg, (const float*)inv_d, kind, is_anchor, (const float*)P,
+               (float*)T, (float*)Q, st.done, st.partials, s, nullptr);
+      } else if (single) {
         k_cg_L<float><<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, (const float*)inv_d,
                                                   kind, (const float*)P, (float*)T, st.done);
         k_cg_LT<float><<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, (const float*)inv_d,

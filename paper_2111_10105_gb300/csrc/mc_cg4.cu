@@ -1,0 +1,327 @@
+// FP32 decoder CG with four columns per thread (the mixed-precision modes).
+//
+// Same iteration, reduction order and results as the scalar FP32 kernels of
+// mc_cg.cu, for column counts W divisible by 4: every load and store moves a
+// float4 (512 bytes per warp per vertex row instead of 128), which keeps
+// enough bytes in flight per SM for these HBM-bound sweeps.  A CTA covers
+// 128 columns x 8 row lanes.  A group of four columns is skipped only when
+// all four have converged; a converged column inside an active group is
+// recomputed harmlessly (its alpha and beta are 0, its dot products unused).
+#include <algorithm>
+
+#include "mc_internal.cuh"
+
+namespace mc {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kCols = 128;
+
+struct Dot2 {   // compensated FP32 dot product (TwoProduct + TwoSum)
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(err, e));
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
+// combine the 8 row lanes' partial sums of this CTA's 128 columns, fixed order
+__device__ __forceinline__ void cta_partials4(const double v[4], double (*sh)[kCols + 1],
+                                              double* out, int W, int col0, bool valid) {
+  const int lane = threadIdx.x & 31, rl = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) sh[rl][lane * 4 + c] = v[c];
+  __syncthreads();
+  if (rl == 0 && valid) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      double s = sh[0][lane * 4 + c];
+#pragma unroll
+      for (int r = 1; r < 8; ++r) s += sh[r][lane * 4 + c];
+      out[(long long)blockIdx.y * W + col0 + c] = s;
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ bool group_done(const int32_t* done, int col0) {
+  return done[col0] && done[col0 + 1] && done[col0 + 2] && done[col0 + 3];
+}
+
+__global__ void __launch_bounds__(kThreads) k4_init(CgGeom g, const double* __restrict__ B,
+                                                    float* __restrict__ X, float* __restrict__ R,
+                                                    float* __restrict__ P,
+                                                    const float* __restrict__ inv_diag,
+                                                    double* __restrict__ partials) {
+  __shared__ double sh[8][kCols + 1];
+  const int col0 = blockIdx.x * kCols + (threadIdx.x & 31) * 4;
+  const int rl = threadIdx.x >> 5;
+  const bool valid = col0 < g.W;
+  const long long r0 = (long long)blockIdx.y * g.rows_per_block;
+  const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
+  Dot2 rz[4], bb[4];
+  if (valid) {
+    for (long long i = r0 + rl; i < r1; i += 8) {
+      const long long e = i * g.W + col0;
+      const float d = inv_diag[i];
+      float b[4], z[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        b[c] = (float)B[e + c];
+        z[c] = b[c] * d;
+        rz[c].add(b[c], z[c]);
+        bb[c].add(b[c], b[c]);
+      }
+      st4(X + e, make_float4(0.f, 0.f, 0.f, 0.f));
+      st4(R + e, make_float4(b[0], b[1], b[2], b[3]));
+      st4(P + e, make_float4(z[0], z[1], z[2], z[3]));
+    }
+  }
+  const long long plane = (long long)g.row_blocks * g.W;
+  double v[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) v[c] = rz[c].value();
+  cta_partials4(v, sh, partials, g.W, col0, valid);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) v[c] = bb[c].value();
+  cta_partials4(v, sh, partials + plane, g.W, col0, valid);
+}
+
+// sum of the neighbours' float4 rows, ascending, loaded four rows at a time
+__device__ __forceinline__ float4 gather4(const float* __restrict__ V, const int32_t* __restrict__ ci,
+                                          int b, int e, int W, int col0) {
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  int p = b;
+  for (; p + 4 <= e; p += 4) {
+    const float4 v0 = ld4(V + (long long)ci[p] * W + col0);
+    const float4 v1 = ld4(V + (long long)ci[p + 1] * W + col0);
+    const float4 v2 = ld4(V + (long long)ci[p + 2] * W + col0);
+    const float4 v3 = ld4(V + (long long)ci[p + 3] * W + col0);
+    acc.x += v0.x; acc.y += v0.y; acc.z += v0.z; acc.w += v0.w;
+    acc.x += v1.x; acc.y += v1.y; acc.z += v1.z; acc.w += v1.w;
+    acc.x += v2.x; acc.y += v2.y; acc.z += v2.z; acc.w += v2.w;
+    acc.x += v3.x; acc.y += v3.y; acc.z += v3.z; acc.w += v3.w;
+  }
+  for (; p < e; ++p) {
+    const float4 v = ld4(V + (long long)ci[p] * W + col0);
+    acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+  }
+  return acc;
+}
+
+// FMA chain sum of w[i] * V[i] over the neighbours, ascending
+__device__ __forceinline__ float4 wgather4(const float* __restrict__ V, const float* __restrict__ w,
+                                           const int32_t* __restrict__ ci, int b, int e, int W,
+                                           int col0) {
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  int p = b;
+  for (; p + 4 <= e; p += 4) {
+    const int c0 = ci[p], c1 = ci[p + 1], c2 = ci[p + 2], c3 = ci[p + 3];
+    const float4 v0 = ld4(V + (long long)c0 * W + col0);
+    const float4 v1 = ld4(V + (long long)c1 * W + col0);
+    const float4 v2 = ld4(V + (long long)c2 * W + col0);
+    const float4 v3 = ld4(V + (long long)c3 * W + col0);
+    const float w0 = w[c0], w1 = w[c1], w2 = w[c2], w3 = w[c3];
+    acc.x = fmaf(w0, v0.x, acc.x); acc.y = fmaf(w0, v0.y, acc.y);
+    acc.z = fmaf(w0, v0.z, acc.z); acc.w = fmaf(w0, v0.w, acc.w);
+    acc.x = fmaf(w1, v1.x, acc.x); acc.y = fmaf(w1, v1.y, acc.y);
+    acc.z = fmaf(w1, v1.z, acc.z); acc.w = fmaf(w1, v1.w, acc.w);
+    acc.x = fmaf(w2, v2.x, acc.x); acc.y = fmaf(w2, v2.y, acc.y);
+    acc.z = fmaf(w2, v2.z, acc.z); acc.w = fmaf(w2, v2.w, acc.w);
+    acc.x = fmaf(w3, v3.x, acc.x); acc.y = fmaf(w3, v3.y, acc.y);
+    acc.z = fmaf(w3, v3.z, acc.z); acc.w = fmaf(w3, v3.w, acc.w);
+  }
+  for (; p < e; ++p) {
+    const int c = ci[p];
+    const float4 v = ld4(V + (long long)c * W + col0);
+    const float wc = w[c];
+    acc.x = fmaf(wc, v.x, acc.x); acc.y = fmaf(wc, v.y, acc.y);
+    acc.z = fmaf(wc, v.z, acc.z); acc.w = fmaf(wc, v.w, acc.w);
+  }
+  return acc;
+}
+
+__global__ void __launch_bounds__(kThreads) k4_L(CgGeom g, const int32_t* __restrict__ row_ptr,
+                                                 const int32_t* __restrict__ col_idx,
+                                                 const int32_t* __restrict__ deg,
+                                                 const float* __restrict__ inv_d, int kind,
+                                                 const float* __restrict__ P,
+                                                 float* __restrict__ T,
+                                                 const int32_t* __restrict__ done) {
+  const int col0 = blockIdx.x * kCols + (threadIdx.x & 31) * 4;
+  const int rl = threadIdx.x >> 5;
+  if (col0 >= g.W || group_done(done, col0)) return;
+  const long long r0 = (long long)blockIdx.y * g.rows_per_block;
+  const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
+  for (long long i = r0 + rl; i < r1; i += 8) {
+    const float4 s = gather4(P, col_idx, row_ptr[i], row_ptr[i + 1], g.W, col0);
+    const float4 p = ld4(P + i * g.W + col0);
+    float4 t;
+    if (kind == 0) {
+      const float a = -inv_d[i];
+      t = make_float4(fmaf(a, s.x, p.x), fmaf(a, s.y, p.y), fmaf(a, s.z, p.z), fmaf(a, s.w, p.w));
+    } else {
+      const float d = (float)deg[i];
+      t = make_float4(fmaf(d, p.x, -s.x), fmaf(d, p.y, -s.y), fmaf(d, p.z, -s.z),
+                      fmaf(d, p.w, -s.w));
+    }
+    st4(T + i * g.W + col0, t);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k4_LT(CgGeom g, const int32_t* __restrict__ row_ptr,
+                                                  const int32_t* __restrict__ col_idx,
+                                                  const int32_t* __restrict__ deg,
+                                                  const float* __restrict__ inv_d, int kind,
+                                                  const uint8_t* __restrict__ is_anchor,
+                                                  const float* __restrict__ T,
+                                                  const float* __restrict__ P,
+                                                  float* __restrict__ Q,
+                                                  const int32_t* __restrict__ done,
+                                                  double* __restrict__ partials) {
+  __shared__ double sh[8][kCols + 1];
+  const int col0 = blockIdx.x * kCols + (threadIdx.x & 31) * 4;
+  const int rl = threadIdx.x >> 5;
+  const bool valid = col0 < g.W && !group_done(done, col0);
+  const long long r0 = (long long)blockIdx.y * g.rows_per_block;
+  const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
+  Dot2 pap[4];
+  if (valid) {
+    for (long long j = r0 + rl; j < r1; j += 8) {
+      const int b = row_ptr[j], e = row_ptr[j + 1];
+      const float4 a = kind == 0 ? wgather4(T, inv_d, col_idx, b, e, g.W, col0)
+                                 : gather4(T, col_idx, b, e, g.W, col0);
+      const float4 t = ld4(T + j * g.W + col0);
+      const float4 p = ld4(P + j * g.W + col0);
+      float q[4];
+      if (kind == 0) {
+        q[0] = t.x - a.x; q[1] = t.y - a.y; q[2] = t.z - a.z; q[3] = t.w - a.w;
+      } else {
+        const float d = (float)deg[j];
+        q[0] = fmaf(d, t.x, -a.x); q[1] = fmaf(d, t.y, -a.y);
+        q[2] = fmaf(d, t.z, -a.z); q[3] = fmaf(d, t.w, -a.w);
+      }
+      if (is_anchor[j]) {
+        q[0] += p.x; q[1] += p.y; q[2] += p.z; q[3] += p.w;
+      }
+      st4(Q + j * g.W + col0, make_float4(q[0], q[1], q[2], q[3]));
+      pap[0].add(p.x, q[0]);
+      pap[1].add(p.y, q[1]);
+      pap[2].add(p.z, q[2]);
+      pap[3].add(p.w, q[3]);
+    }
+  }
+  double v[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) v[c] = pap[c].value();
+  cta_partials4(v, sh, partials, g.W, col0, col0 < g.W);
+}
+
+__global__ void __launch_bounds__(kThreads) k4_update(CgGeom g, float* __restrict__ X,
+                                                      float* __restrict__ R,
+                                                      const float* __restrict__ P,
+                                                      const float* __restrict__ Q,
+                                                      const float* __restrict__ inv_diag,
+                                                      const double* __restrict__ alpha,
+                                                      const int32_t* __restrict__ done,
+                                                      double* __restrict__ partials) {
+  __shared__ double sh[8][kCols + 1];
+  const int col0 = blockIdx.x * kCols + (threadIdx.x & 31) * 4;
+  const int rl = threadIdx.x >> 5;
+  const bool valid = col0 < g.W && !group_done(done, col0);
+  const long long r0 = (long long)blockIdx.y * g.rows_per_block;
+  const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
+  Dot2 rz[4], rr[4];
+  if (valid) {
+    const float a0 = (float)alpha[col0], a1 = (float)alpha[col0 + 1];
+    const float a2 = (float)alpha[col0 + 2], a3 = (float)alpha[col0 + 3];
+    for (long long i = r0 + rl; i < r1; i += 8) {
+      const long long e = i * g.W + col0;
+      const float4 x = ld4(X + e), r = ld4(R + e), p = ld4(P + e), q = ld4(Q + e);
+      const float d = inv_diag[i];
+      st4(X + e, make_float4(fmaf(a0, p.x, x.x), fmaf(a1, p.y, x.y), fmaf(a2, p.z, x.z),
+                             fmaf(a3, p.w, x.w)));
+      const float4 rn = make_float4(fmaf(-a0, q.x, r.x), fmaf(-a1, q.y, r.y), fmaf(-a2, q.z, r.z),
+                                    fmaf(-a3, q.w, r.w));
+      st4(R + e, rn);
+      rz[0].add(rn.x, rn.x * d); rr[0].add(rn.x, rn.x);
+      rz[1].add(rn.y, rn.y * d); rr[1].add(rn.y, rn.y);
+      rz[2].add(rn.z, rn.z * d); rr[2].add(rn.z, rn.z);
+      rz[3].add(rn.w, rn.w * d); rr[3].add(rn.w, rn.w);
+    }
+  }
+  const long long plane = (long long)g.row_blocks * g.W;
+  double v[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) v[c] = rz[c].value();
+  cta_partials4(v, sh, partials, g.W, col0, col0 < g.W);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) v[c] = rr[c].value();
+  cta_partials4(v, sh, partials + plane, g.W, col0, col0 < g.W);
+}
+
+__global__ void __launch_bounds__(kThreads) k4_dir(CgGeom g, const float* __restrict__ R,
+                                                   float* __restrict__ P,
+                                                   const float* __restrict__ inv_diag,
+                                                   const double* __restrict__ beta,
+                                                   const int32_t* __restrict__ done) {
+  const int col0 = blockIdx.x * kCols + (threadIdx.x & 31) * 4;
+  const int rl = threadIdx.x >> 5;
+  if (col0 >= g.W || group_done(done, col0)) return;
+  const float b0 = (float)beta[col0], b1 = (float)beta[col0 + 1];
+  const float b2 = (float)beta[col0 + 2], b3 = (float)beta[col0 + 3];
+  const long long r0 = (long long)blockIdx.y * g.rows_per_block;
+  const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
+  for (long long i = r0 + rl; i < r1; i += 8) {
+    const long long e = i * g.W + col0;
+    const float4 r = ld4(R + e), p = ld4(P + e);
+    const float d = inv_diag[i];
+    st4(P + e, make_float4(fmaf(b0, p.x, r.x * d), fmaf(b1, p.y, r.y * d), fmaf(b2, p.z, r.z * d),
+                           fmaf(b3, p.w, r.w * d)));
+  }
+}
+
+}  // namespace
+
+bool cg4_applies(int W, int single) { return single && (W % 4) == 0; }
+
+void cg4_init(const CgGeom& g, const double* B, float* X, float* R, float* P,
+              const float* inv_diag, double* partials, cudaStream_t s) {
+  dim3 grid((g.W + kCols - 1) / kCols, g.row_blocks);
+  k4_init<<<grid, kThreads, 0, s>>>(g, B, X, R, P, inv_diag, partials);
+}
+
+void cg4_op(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* deg,
+            const float* inv_d, int kind, const uint8_t* is_anchor, const float* P, float* T,
+            float* Q, const int32_t* done, double* partials, cudaStream_t s, cudaEvent_t* ev) {
+  dim3 grid((g.W + kCols - 1) / kCols, g.row_blocks);
+  k4_L<<<grid, kThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, P, T, done);
+  if (ev) cudaEventRecord(ev[1], s);
+  k4_LT<<<grid, kThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, is_anchor, T, P, Q,
+                                  done, partials);
+}
+
+void cg4_update(const CgGeom& g, float* X, float* R, const float* P, const float* Q,
+                const float* inv_diag, const double* alpha, const int32_t* done,
+                double* partials, cudaStream_t s) {
+  dim3 grid((g.W + kCols - 1) / kCols, g.row_blocks);
+  k4_update<<<grid, kThreads, 0, s>>>(g, X, R, P, Q, inv_diag, alpha, done, partials);
+}
+
+void cg4_dir(const CgGeom& g, const float* R, float* P, const float* inv_diag, const double* beta,
+             const int32_t* done, cudaStream_t s) {
+  dim3 grid((g.W + kCols - 1) / kCols, g.row_blocks);
+  k4_dir<<<grid, kThreads, 0, s>>>(g, R, P, inv_diag, beta, done);
+}
+
+}  // namespace mc

@@ -192,6 +192,18 @@ void cg_iteration(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_id
                   double rtol, int max_iters, CgState& st, int single, cudaStream_t s,
                   Launches& L, cudaEvent_t* ev /* 7 events around the 6 kernels, or null */);
 void widen(const float* X, long long count, double* out, cudaStream_t s, Launches& L);
+// FP32 CG with four columns per thread (W % 4 == 0), mc_cg4.cu
+bool cg4_applies(int W, int single);
+void cg4_init(const CgGeom& g, const double* B, float* X, float* R, float* P,
+              const float* inv_diag, double* partials, cudaStream_t s);
+void cg4_op(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* deg,
+            const float* inv_d, int kind, const uint8_t* is_anchor, const float* P, float* T,
+            float* Q, const int32_t* done, double* partials, cudaStream_t s, cudaEvent_t* ev);
+void cg4_update(const CgGeom& g, float* X, float* R, const float* P, const float* Q,
+                const float* inv_diag, const double* alpha, const int32_t* done,
+                double* partials, cudaStream_t s);
+void cg4_dir(const CgGeom& g, const float* R, float* P, const float* inv_diag, const double* beta,
+             const int32_t* done, cudaStream_t s);
 void narrow(const double* X, long long count, float* out, cudaStream_t s, Launches& L);
 constexpr int kCgKernels = 6;
 extern const char* const kCgKernelNames[kCgKernels];
