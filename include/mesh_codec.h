@@ -177,6 +177,37 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_encode(mesh_codec_t* h, const doub
 MESH_CODEC_API mesh_codec_status_t mesh_codec_decode(mesh_codec_t* h, const uint8_t* bitstream, size_t bytes,
                                       double* positions_out, void* stream);
 
+/* Decoder with a warm start: `x0` (device float64 [F][n][3], or NULL for the
+ * cold start X0 = 0) is the first iterate of the CG solve of Eq. 12, e.g. the
+ * previous segment's reconstruction or a learned prediction of it.  The
+ * result is the same least-squares solution; only the iteration count
+ * changes.  Needs solve_mode FRAMES (the factored solve has no X iterate).
+ * Errors: as mesh_codec_decode, MC_E_INVALID_ARG for a misaligned x0 or a
+ * factored handle. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_decode_ex(mesh_codec_t* h, const uint8_t* bitstream,
+                                                        size_t bytes, const double* x0,
+                                                        double* positions_out, void* stream);
+
+/* The first stage of the decoder alone: unpack and dequantize the stream
+ * (Eq. 10) and, when `delta_out` is not NULL, back-project the delta
+ * coordinates (Eq. 11) into it (device float64 [n][3F], vertex-major,
+ * column c*F + f); when `anchors_out` is not NULL, copy the dequantized
+ * anchor positions there (device float64 [3][n_c][F]).  No solve.  Lets a
+ * caller build a warm start for mesh_codec_decode_ex from what the stream
+ * carries.  Synchronises `stream`.  Errors: as mesh_codec_decode. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_decode_stage(mesh_codec_t* h, const uint8_t* bitstream,
+                                                           size_t bytes, double* delta_out,
+                                                           double* anchors_out, void* stream);
+
+/* Start basis of the orthogonal iterations (Algorithm 1).  `q0`: device
+ * float64 [3][F][k], made orthonormal (CholeskyQR3) and used by every
+ * following encode, e.g. the previous block's dictionary U[i-1] as
+ * Algorithm 1 does for blocks 2..n_b; NULL restores the seeded random start.
+ * Synchronises `stream`.  Errors: MC_E_INVALID_ARG, MC_E_NUMERICAL (rank-
+ * deficient q0), MC_E_CUDA. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_set_start_basis(mesh_codec_t* h, const double* q0,
+                                                              void* stream);
+
 /* Same as encode / decode with HOST buffers: the call copies the input to
  * the device, runs the codec and copies the result back before returning.
  * Host memory may be pageable; pinned memory copies faster. */
@@ -313,6 +344,151 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_adjacency_static(const int32_t* tr
 /* Frees the handle and its workspace (synchronises the device first).
  * NULL is accepted. */
 MESH_CODEC_API void mesh_codec_destroy(mesh_codec_t* h);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start for the decoder.  The paper has no counterpart: its
+ * decoder solves Eq. 12 from scratch.  A small perceptron predicts each
+ * segment's positions from the previous segment's reconstruction and the
+ * current segment's anchors and delta coordinates; the prediction is passed
+ * to mesh_codec_decode_ex as the CG's first iterate, so it changes only the
+ * iteration count, never the solution.
+ *
+ * Network: n_in -> n_hidden -> n_hidden -> n_out on standardised inputs
+ * (mesh_codec_mlp_fit_normalizer), ReLU after the two hidden layers, none
+ * after the output.  Parameters are one flat float32 array
+ * [W1 (n_hidden x n_in, row-major), b1, W2 (n_hidden x n_hidden), b2,
+ *  W3 (n_out x n_hidden), b3]; every product uses a bfloat16 copy of the
+ * weights (round to nearest even) with float32 accumulation; biases stay
+ * float32.  Training minimises the mean squared error over all outputs with
+ * Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the float32 master copy.
+ * Samples are rows: X [N][n_in], targets and outputs [N][n_out], float32,
+ * device memory, row-major.  One handle is not safe for concurrent calls.
+ * ---------------------------------------------------------------------- */
+typedef struct mesh_codec_mlp mesh_codec_mlp_t;
+
+/* Allocates a network with He-uniform weights drawn from splitmix64(seed)
+ * (output layer scaled by 0.1) and zero biases; synchronises the device.
+ * Sizes 1..4096.  Errors: MC_E_INVALID_ARG, MC_E_OOM, MC_E_CUDA. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_mlp_create(int n_in, int n_hidden, int n_out,
+                                                         uint64_t seed, mesh_codec_mlp_t** out);
+
+/* Number of float32 parameters (0 for NULL). */
+MESH_CODEC_API size_t mesh_codec_mlp_param_count(const mesh_codec_mlp_t* m);
+
+/* Copies parameter_count floats to device `dst`: which = 0 the float32
+ * master parameters, 1 the bfloat16 copy widened to float32, 2 the gradient
+ * of the last mesh_codec_mlp_train_step.  Errors: MC_E_INVALID_ARG, MC_E_CUDA. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_mlp_get_params(const mesh_codec_mlp_t* m, int which,
+                                                             float* dst, void* stream);
+
+/* Replaces the master parameters (device float32, parameter_count values),
+ * refreshes the bfloat16 copy and resets Adam's moments and step count.
+ * Errors: MC_E_INVALID_ARG, MC_E_CUDA. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_mlp_set_params(mesh_codec_mlp_t* m, const float* src,
+                                                             void* stream);
+
+/* Y = network(X) for N rows, enqueued on `stream`.  Grows the handle's
+ * activation buffers to N rows on first use of a larger N (cudaMalloc).
+ * Errors: MC_E_INVALID_ARG, MC_E_OOM, MC_E_CUDA. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_mlp_forward(mesh_codec_mlp_t* m, const float* X,
+                                                          long long N, float* Y, void* stream);
+
+/* Forward pass, loss mean((Y - T)^2) and its gradient for N rows; with
+ * update != 0 one Adam step of learning rate lr.  `loss` (host, may be
+ * NULL) receives the loss, which synchronises `stream`.
+ * Errors: MC_E_INVALID_ARG, MC_E_OOM, MC_E_CUDA. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_mlp_train_step(mesh_codec_mlp_t* m, const float* X,
+                                                             const float* T, long long N, float lr,
+                                                             int update, double* loss,
+                                                             void* stream);
+
+/* Input standardisation: the network reads x' = (x - mu) * inv_sigma per
+ * feature (float32), identity (mu 0, inv_sigma 1) until fitted.  Fitting
+ * sets mu to the column means of X [N][n_in] and inv_sigma to 1 / the
+ * population standard deviation (sums in float64; a column with standard
+ * deviation <= 1e-12 * max(1, |mean|) keeps inv_sigma = 1).
+ * Errors: MC_E_INVALID_ARG, MC_E_CUDA. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_mlp_fit_normalizer(mesh_codec_mlp_t* m,
+                                                                 const float* X, long long N,
+                                                                 void* stream);
+/* Copies mu and inv_sigma (n_in float32 each) to device memory. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_mlp_get_normalizer(const mesh_codec_mlp_t* m,
+                                                                 float* mu, float* inv_sigma,
+                                                                 void* stream);
+
+/* Check mode: fp32_weights = 1 makes every product read the float32 master
+ * weights instead of the bfloat16 copy (for gradient checks against a
+ * float64 reference); 0 (the default) restores bfloat16.
+ * Errors: MC_E_INVALID_ARG. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_mlp_set_check_mode(mesh_codec_mlp_t* m,
+                                                                 int fp32_weights);
+
+/* Frees the network (synchronises the device first).  NULL is accepted. */
+MESH_CODEC_API void mesh_codec_mlp_destroy(mesh_codec_mlp_t* m);
+
+/* For each vertex v of a rest pose `rest` (device float64 [n][3]) the
+ * indices into `anchors` (device int32 [n_c]) of its MESH_CODEC_WARM_ANCHORS
+ * nearest anchors in Euclidean distance, nearest first (equal distances:
+ * the lower index first; with fewer anchors the last one repeats), written
+ * to nearest[v][j] (int32), and those distances to dist[v][j] (float32).
+ * Errors: MC_E_INVALID_ARG, MC_E_CUDA. */
+#define MESH_CODEC_WARM_ANCHORS 3
+#define MESH_CODEC_WARM_FEATURES 16
+MESH_CODEC_API mesh_codec_status_t mesh_codec_nearest_anchor(int n, int n_c, const double* rest,
+                                                             const int32_t* anchors,
+                                                             int32_t* nearest, float* dist,
+                                                             void* stream);
+
+/* Warm-start features of segment s from what its stream carries and the
+ * decoded segment s-1: MESH_CODEC_WARM_FEATURES float32 per sample, sample
+ * index e = f*n + v, for the nearest anchors a_j = nearest[v][j]:
+ *   [4j .. 4j+2] a_cur(a_j, f) - x_last(anchors[a_j])   (j = 0, 1, 2)
+ *   [4j + 3]     dist[v][j]
+ *   [12 .. 14]   (delta_cur(v, f) - delta_prev(v, F-1)) * dscale
+ *   [15]         (f + 1) / F
+ * x_last: the last decoded frame of segment s-1, device float64 [n][3].
+ * a_cur: the dequantized anchor positions of segment s, [3][n_c][F];
+ * delta_cur, delta_prev: the back-projected delta coordinates of segments s
+ * and s-1, vertex-major [n][3F] (column c*F + f), as mesh_codec_decode_stage
+ * returns them.  With x_cur ([F][n][3]) != NULL also writes the regression
+ * target target[e][c] = x_cur(v, f) - x_last(v) (float32 [n*F][3]).
+ * Each difference is formed in float64 and rounded once to float32.
+ * Errors: MC_E_INVALID_ARG, MC_E_CUDA. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_warm_features(
+    int n, int F, int n_c, const double* x_last, const double* a_cur, const int32_t* anchors,
+    const int32_t* nearest, const float* dist, const double* delta_cur, const double* delta_prev,
+    float dscale, const double* x_cur, float* features, float* target, void* stream);
+
+/* Decoder start from a prediction: x0(f, v, c) = x_last(v, c) + pred[f*n + v][c]
+ * (float64 [F][n][3]); pred (float32 [n*F][3]) may be NULL for the plain
+ * previous-frame start.  Errors: MC_E_INVALID_ARG, MC_E_CUDA. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_warm_compose(int n, int F, const double* x_last,
+                                                           const float* pred, double* x0,
+                                                           void* stream);
+
+/* Training minibatch: out[i][:] = X[r_i][:] for i < count, rows of `width`
+ * float32, r_i = splitmix64(seed) output i modulo N.  Equal seeds draw equal
+ * rows, so features and targets are sampled by two calls with one seed.
+ * Errors: MC_E_INVALID_ARG, MC_E_CUDA. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_sample_rows(const float* X, int width, long long N,
+                                                          uint64_t seed, long long count,
+                                                          float* out, void* stream);
+
+/* Basis head of the warm start (the encoder's Algorithm 1 start).  Row
+ * r = c*F + f of the previous segment's dictionary U_prev (device float64
+ * [3][F][k], as MC_BUF_BASIS holds it) gives the features
+ * [U_prev(c, f, 0..k-1), (f + 1) / F] (float32 [3F][k+1]); with U_cur !=
+ * NULL also the target U_cur - U_prev (float32 [3F][k]).
+ * Errors: MC_E_INVALID_ARG, MC_E_CUDA. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_basis_features(int F, int k, const double* U_prev,
+                                                             const double* U_cur, float* features,
+                                                             float* target, void* stream);
+
+/* q0 = U_prev + pred (float64 [3][F][k]; pred float32 [3F][k] or NULL), to
+ * pass to mesh_codec_set_start_basis.  Errors: MC_E_INVALID_ARG, MC_E_CUDA. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_basis_compose(int F, int k, const double* U_prev,
+                                                            const float* pred, double* q0,
+                                                            void* stream);
 
 #ifdef __cplusplus
 }

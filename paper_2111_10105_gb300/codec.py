@@ -93,6 +93,32 @@ _SIGS = {
     "mesh_codec_encode": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t,
                                          ctypes.POINTER(ctypes.c_size_t), _P]),
     "mesh_codec_decode": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, _P]),
+    "mesh_codec_decode_ex": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, _P, _P]),
+    "mesh_codec_set_start_basis": (ctypes.c_int, [_P, _P, _P]),
+    "mesh_codec_decode_stage": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, _P, _P]),
+    "mesh_codec_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_uint64, ctypes.POINTER(_P)]),
+    "mesh_codec_mlp_param_count": (ctypes.c_size_t, [_P]),
+    "mesh_codec_mlp_get_params": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "mesh_codec_mlp_set_params": (ctypes.c_int, [_P, _P, _P]),
+    "mesh_codec_mlp_forward": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P, _P]),
+    "mesh_codec_mlp_train_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, ctypes.c_float,
+                                                 ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                                 _P]),
+    "mesh_codec_mlp_set_check_mode": (ctypes.c_int, [_P, ctypes.c_int]),
+    "mesh_codec_mlp_fit_normalizer": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P]),
+    "mesh_codec_mlp_get_normalizer": (ctypes.c_int, [_P, _P, _P, _P]),
+    "mesh_codec_mlp_destroy": (None, [_P]),
+    "mesh_codec_nearest_anchor": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, _P, _P,
+                                                 _P]),
+    "mesh_codec_warm_features": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P,
+                                                _P, _P, _P, _P, _P, ctypes.c_float, _P, _P, _P,
+                                                _P]),
+    "mesh_codec_warm_compose": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
+    "mesh_codec_sample_rows": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_longlong, ctypes.c_uint64,
+                                              ctypes.c_longlong, _P, _P]),
+    "mesh_codec_basis_features": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]),
+    "mesh_codec_basis_compose": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
     "mesh_codec_encode_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t,
                                               ctypes.POINTER(ctypes.c_size_t), _P]),
     "mesh_codec_decode_host": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, _P]),
@@ -213,17 +239,50 @@ class MeshCodec:
         _check(st, "mesh_codec_encode")
         return out[: written.value]
 
-    def decode(self, bitstream, out=None, stream=None, allow_not_converged=False):
+    def decode(self, bitstream, out=None, stream=None, allow_not_converged=False, x0=None):
+        """bitstream: CUDA uint8 -> CUDA float64 [F, n, 3].  x0 (CUDA float64
+        [F, n, 3], frames solve only) is the CG's first iterate."""
         torch = _torch()
         assert bitstream.is_cuda and bitstream.dtype == torch.uint8
         if out is None:
             out = torch.empty((self.F, self.n, 3), dtype=torch.float64, device=bitstream.device)
-        st = self._lib.mesh_codec_decode(self._h, ctypes.c_void_p(bitstream.data_ptr()),
-                                         bitstream.numel(), ctypes.c_void_p(out.data_ptr()),
-                                         _stream_ptr(stream))
+        x0p = None
+        if x0 is not None:
+            assert x0.is_cuda and x0.dtype == torch.float64 and x0.is_contiguous()
+            assert tuple(x0.shape) == (self.F, self.n, 3)
+            x0p = ctypes.c_void_p(x0.data_ptr())
+        st = self._lib.mesh_codec_decode_ex(self._h, ctypes.c_void_p(bitstream.data_ptr()),
+                                            bitstream.numel(), x0p,
+                                            ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream))
         if not (allow_not_converged and st == 6):
             _check(st, "mesh_codec_decode")
         return out
+
+    def decode_stage(self, bitstream, stream=None):
+        """Unpack + back-projection only: (delta~ [n, 3F] vertex-major,
+        dequantized anchor positions [3, n_c, F]) as CUDA float64 tensors."""
+        torch = _torch()
+        assert bitstream.is_cuda and bitstream.dtype == torch.uint8
+        n_c = self.params.n_anchors
+        delta = torch.empty((self.n, 3 * self.F), dtype=torch.float64, device=bitstream.device)
+        anc = torch.empty((3, max(n_c, 1), self.F), dtype=torch.float64, device=bitstream.device)
+        st = self._lib.mesh_codec_decode_stage(self._h, ctypes.c_void_p(bitstream.data_ptr()),
+                                               bitstream.numel(), ctypes.c_void_p(delta.data_ptr()),
+                                               ctypes.c_void_p(anc.data_ptr()), _stream_ptr(stream))
+        _check(st, "mesh_codec_decode_stage")
+        return delta, anc[:, :n_c]
+
+    def set_start_basis(self, q0=None, stream=None):
+        """Orthogonal-iteration start basis: CUDA float64 [3, F, k] (made
+        orthonormal), or None for the seeded random start."""
+        ptr = None
+        if q0 is not None:
+            torch = _torch()
+            assert q0.is_cuda and q0.dtype == torch.float64 and q0.is_contiguous()
+            assert tuple(q0.shape) == (3, self.F, self.k)
+            ptr = ctypes.c_void_p(q0.data_ptr())
+        _check(self._lib.mesh_codec_set_start_basis(self._h, ptr, _stream_ptr(stream)),
+               "mesh_codec_set_start_basis")
 
     # ------------------------------------------------------------ host API
     def encode_host(self, positions, out=None, stream=None):
@@ -384,3 +443,191 @@ def decode_batch(codecs, bitstreams, outs=None, stream=None, allow_not_converged
     if not (allow_not_converged and st == 6):
         _check(st, "mesh_codec_decode_batch")
     return outs
+
+
+# ---------------------------------------------------------------- learned warm start
+def _dptr(t, dtype=None, shape=None):
+    torch = _torch()
+    assert t.is_cuda and t.is_contiguous(), "CUDA contiguous tensor expected"
+    if dtype is not None:
+        assert t.dtype == dtype, f"{t.dtype} != {dtype}"
+    if shape is not None:
+        assert tuple(t.shape) == tuple(shape), f"{tuple(t.shape)} != {tuple(shape)}"
+    del torch
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Mlp:
+    """n_in -> n_hidden -> n_hidden -> n_out perceptron (ReLU), bfloat16
+    weights, float32 accumulation, trained with Adam on a float32 master
+    copy; see mesh_codec_mlp_create.  Rows are samples (float32 CUDA)."""
+
+    def __init__(self, n_in, n_hidden=256, n_out=3, seed=0):
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        _check(self._lib.mesh_codec_mlp_create(int(n_in), int(n_hidden), int(n_out),
+                                               ctypes.c_uint64(seed & ((1 << 64) - 1)),
+                                               ctypes.byref(h)), "mesh_codec_mlp_create")
+        self._h = h
+        self.n_in, self.n_hidden, self.n_out = int(n_in), int(n_hidden), int(n_out)
+        self.count = int(self._lib.mesh_codec_mlp_param_count(h))
+
+    def params(self, which=0, stream=None):
+        """0: float32 master, 1: bfloat16 copy (as float32), 2: last gradient."""
+        torch = _torch()
+        out = torch.empty(self.count, dtype=torch.float32, device="cuda")
+        _check(self._lib.mesh_codec_mlp_get_params(self._h, int(which), _dptr(out),
+                                                   _stream_ptr(stream)),
+               "mesh_codec_mlp_get_params")
+        return out
+
+    def set_params(self, flat, stream=None):
+        torch = _torch()
+        _check(self._lib.mesh_codec_mlp_set_params(self._h, _dptr(flat, torch.float32,
+                                                                   (self.count,)),
+                                                   _stream_ptr(stream)),
+               "mesh_codec_mlp_set_params")
+
+    def fit_normalizer(self, X, stream=None):
+        """Standardise inputs by the column means / deviations of X."""
+        torch = _torch()
+        _check(self._lib.mesh_codec_mlp_fit_normalizer(
+            self._h, _dptr(X, torch.float32, (X.shape[0], self.n_in)), X.shape[0],
+            _stream_ptr(stream)), "mesh_codec_mlp_fit_normalizer")
+
+    def normalizer(self, stream=None):
+        torch = _torch()
+        mu = torch.empty(self.n_in, dtype=torch.float32, device="cuda")
+        inv = torch.empty(self.n_in, dtype=torch.float32, device="cuda")
+        _check(self._lib.mesh_codec_mlp_get_normalizer(self._h, _dptr(mu), _dptr(inv),
+                                                       _stream_ptr(stream)),
+               "mesh_codec_mlp_get_normalizer")
+        return mu, inv
+
+    def set_check_mode(self, fp32_weights):
+        _check(self._lib.mesh_codec_mlp_set_check_mode(self._h, int(bool(fp32_weights))),
+               "mesh_codec_mlp_set_check_mode")
+
+    def forward(self, X, out=None, stream=None):
+        torch = _torch()
+        N = X.shape[0]
+        if out is None:
+            out = torch.empty((N, self.n_out), dtype=torch.float32, device=X.device)
+        _check(self._lib.mesh_codec_mlp_forward(self._h, _dptr(X, torch.float32, (N, self.n_in)),
+                                                N, _dptr(out, torch.float32, (N, self.n_out)),
+                                                _stream_ptr(stream)),
+               "mesh_codec_mlp_forward")
+        return out
+
+    def train_step(self, X, T, lr=1e-3, update=True, want_loss=True, stream=None):
+        """One forward/backward pass (and an Adam step when update); returns
+        the mean squared error (synchronising) or None."""
+        torch = _torch()
+        N = X.shape[0]
+        loss = ctypes.c_double()
+        _check(self._lib.mesh_codec_mlp_train_step(
+            self._h, _dptr(X, torch.float32, (N, self.n_in)),
+            _dptr(T, torch.float32, (N, self.n_out)), N, float(lr), int(bool(update)),
+            ctypes.byref(loss) if want_loss else None, _stream_ptr(stream)),
+            "mesh_codec_mlp_train_step")
+        return loss.value if want_loss else None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mesh_codec_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+WARM_ANCHORS = 3
+WARM_FEATURES = 16
+
+
+def nearest_anchors(rest, anchors, stream=None):
+    """rest: CUDA float64 [n, 3]; anchors: CUDA int32 [n_c] ->
+    (int32 [n, 3] indices into anchors, float32 [n, 3] distances)."""
+    torch = _torch()
+    n, n_c = rest.shape[0], anchors.shape[0]
+    idx = torch.empty((n, WARM_ANCHORS), dtype=torch.int32, device=rest.device)
+    dist = torch.empty((n, WARM_ANCHORS), dtype=torch.float32, device=rest.device)
+    _check(load_library().mesh_codec_nearest_anchor(
+        n, n_c, _dptr(rest, torch.float64, (n, 3)), _dptr(anchors, torch.int32, (n_c,)),
+        _dptr(idx), _dptr(dist), _stream_ptr(stream)), "mesh_codec_nearest_anchor")
+    return idx, dist
+
+
+def warm_features(x_last, a_cur, anchors, nearest, dist, delta_cur, delta_prev, dscale=1.0,
+                  x_cur=None, stream=None):
+    """Features (float32 [F*n, 16]) and, with x_cur, targets (float32
+    [F*n, 3]); see mesh_codec_warm_features for the layouts."""
+    torch = _torch()
+    n = x_last.shape[0]
+    n_c, F = a_cur.shape[1], a_cur.shape[2]
+    a_cur = a_cur.contiguous()
+    feat = torch.empty((n * F, WARM_FEATURES), dtype=torch.float32, device=x_last.device)
+    tgt = None
+    if x_cur is not None:
+        tgt = torch.empty((n * F, 3), dtype=torch.float32, device=x_last.device)
+    f64 = torch.float64
+    _check(load_library().mesh_codec_warm_features(
+        n, F, n_c, _dptr(x_last, f64, (n, 3)), _dptr(a_cur, f64, (3, n_c, F)),
+        _dptr(anchors, torch.int32, (n_c,)), _dptr(nearest, torch.int32, (n, WARM_ANCHORS)),
+        _dptr(dist, torch.float32, (n, WARM_ANCHORS)), _dptr(delta_cur, f64, (n, 3 * F)),
+        _dptr(delta_prev, f64, (n, 3 * F)), float(dscale),
+        None if x_cur is None else _dptr(x_cur, f64, (F, n, 3)), _dptr(feat),
+        None if tgt is None else _dptr(tgt), _stream_ptr(stream)), "mesh_codec_warm_features")
+    return feat, tgt
+
+
+def warm_compose(x_last, F, pred=None, stream=None):
+    """x0 [F, n, 3] float64 = x_last (+ pred reshaped to [F, n, 3])."""
+    torch = _torch()
+    n = x_last.shape[0]
+    x0 = torch.empty((F, n, 3), dtype=torch.float64, device=x_last.device)
+    _check(load_library().mesh_codec_warm_compose(
+        n, F, _dptr(x_last, torch.float64, (n, 3)),
+        None if pred is None else _dptr(pred, torch.float32, (n * F, 3)), _dptr(x0),
+        _stream_ptr(stream)), "mesh_codec_warm_compose")
+    return x0
+
+
+def sample_rows(X, seed, count, stream=None):
+    """Rows splitmix64(seed)_i mod N of a float32 [N, w] CUDA tensor."""
+    torch = _torch()
+    N, w = X.shape
+    out = torch.empty((int(count), w), dtype=torch.float32, device=X.device)
+    _check(load_library().mesh_codec_sample_rows(_dptr(X, torch.float32), w, N,
+                                                 ctypes.c_uint64(seed & ((1 << 64) - 1)),
+                                                 int(count), _dptr(out), _stream_ptr(stream)),
+           "mesh_codec_sample_rows")
+    return out
+
+
+def basis_features(U_prev, U_cur=None, stream=None):
+    """U [3, F, k] float64 -> (features float32 [3F, k+1], target [3F, k] or None)."""
+    torch = _torch()
+    _, F, k = U_prev.shape
+    feat = torch.empty((3 * F, k + 1), dtype=torch.float32, device=U_prev.device)
+    tgt = None if U_cur is None else torch.empty((3 * F, k), dtype=torch.float32,
+                                                 device=U_prev.device)
+    _check(load_library().mesh_codec_basis_features(
+        F, k, _dptr(U_prev, torch.float64, (3, F, k)),
+        None if U_cur is None else _dptr(U_cur, torch.float64, (3, F, k)), _dptr(feat),
+        None if tgt is None else _dptr(tgt), _stream_ptr(stream)), "mesh_codec_basis_features")
+    return feat, tgt
+
+
+def basis_compose(U_prev, pred=None, stream=None):
+    torch = _torch()
+    _, F, k = U_prev.shape
+    q0 = torch.empty((3, F, k), dtype=torch.float64, device=U_prev.device)
+    _check(load_library().mesh_codec_basis_compose(
+        F, k, _dptr(U_prev, torch.float64, (3, F, k)),
+        None if pred is None else _dptr(pred, torch.float32, (3 * F, k)), _dptr(q0),
+        _stream_ptr(stream)), "mesh_codec_basis_compose")
+    return q0

@@ -493,7 +493,8 @@ __global__ void k_flag_not_converged(const int32_t* done, int W, uint32_t* statu
 // Decoder, in three phases so that several handles can advance their CG
 // solves in lockstep on their own streams (mesh_codec_decode_batch).
 // Phase 1: unpack, back-projection, right-hand sides, CG start.
-static void decode_prepare(mesh_codec* h, const uint8_t* in, cudaStream_t s, Launches& L) {
+static void decode_prepare(mesh_codec* h, const uint8_t* in, cudaStream_t s, Launches& L,
+                           const double* x0 = nullptr) {
   const int n = h->n, F = h->F, k = h->k, W = h->W;
   DecodeState& d = h->dec;
   cudaMemsetAsync(h->d_status, 0, sizeof(uint32_t), s);
@@ -552,7 +553,18 @@ static void decode_prepare(mesh_codec* h, const uint8_t* in, cudaStream_t s, Lau
     }
     d.geom = h->tuned;
   }
-  cg_init(d.geom, h->B, h->X, h->R, h->P, d.inv_diag, h->cg, d.single, s, L);
+  if (x0 && !d.factored) {
+    // warm start: the caller's X0 [F][n][3] as the CG's first iterate
+    frames_to_vertex_major(x0, h->D, F, n, s, L);
+    if (d.single)
+      narrow(h->D, (long long)n * W, (float*)h->X, s, L);
+    else
+      cudaMemcpyAsync(h->X, h->D, sizeof(double) * n * W, cudaMemcpyDeviceToDevice, s);
+    cg_init_warm(d.geom, h->row_ptr, h->col_idx, h->deg, d.inv_d, h->is_anchor, h->kind, h->B,
+                 h->X, h->R, h->P, h->Tv, h->Qv, d.inv_diag, h->cg, d.single, s, L);
+  } else {
+    cg_init(d.geom, h->B, h->X, h->R, h->P, d.inv_diag, h->cg, d.single, s, L);
+  }
   h->cg_columns = d.Wc;
   d.it = 0;
 }
@@ -643,8 +655,9 @@ static void decode_finish(mesh_codec* h, double* out, cudaStream_t s, Launches& 
 }
 
 static mesh_codec_status_t enqueue_decode(mesh_codec* h, const uint8_t* in, double* out,
-                                          cudaStream_t s, Launches& L) {
-  decode_prepare(h, in, s, L);
+                                          cudaStream_t s, Launches& L,
+                                          const double* x0 = nullptr) {
+  decode_prepare(h, in, s, L, x0);
   while (decode_cg_chunk(h, 32, s, L)) {
     MC_TRY(cudaStreamSynchronize(s));
     if (*h->h_active == 0) break;
@@ -660,7 +673,13 @@ __global__ void k_flag_not_converged(const int32_t* done, int W, uint32_t* statu
 
 mesh_codec_status_t mesh_codec_decode(mesh_codec_t* h, const uint8_t* bitstream, size_t bytes,
                                       double* positions_out, void* stream) {
+  return mesh_codec_decode_ex(h, bitstream, bytes, nullptr, positions_out, stream);
+}
+
+mesh_codec_status_t mesh_codec_decode_ex(mesh_codec_t* h, const uint8_t* bitstream, size_t bytes,
+                                         const double* x0, double* positions_out, void* stream) {
   if (!h || !bitstream || !positions_out) return MC_E_INVALID_ARG;
+  if (x0 && (((uintptr_t)x0 & 7) || use_factored(h))) return MC_E_INVALID_ARG;
   if (((uintptr_t)bitstream & 7) || ((uintptr_t)positions_out & 7)) return MC_E_INVALID_ARG;
   if (bytes < 64) return MC_E_BITSTREAM_CORRUPT;
   if (h->n_c == 0) return MC_E_INVALID_ARG;   // Eq. 12 needs anchors (L is singular)
@@ -672,12 +691,66 @@ mesh_codec_status_t mesh_codec_decode(mesh_codec_t* h, const uint8_t* bitstream,
   if (st != MC_OK) return st;
   h->launches_decode = 0;
   Launches L{&h->launches_decode};
-  st = enqueue_decode(h, bitstream, positions_out, s, L);
+  st = enqueue_decode(h, bitstream, positions_out, s, L, x0);
   if (st != MC_OK) return st;
   MC_TRY(cudaGetLastError());
   st = read_status(h, s);
   prof_collect(h);
   return st;
+}
+
+mesh_codec_status_t mesh_codec_decode_stage(mesh_codec_t* h, const uint8_t* bitstream,
+                                            size_t bytes, double* delta_out, double* anchors_out,
+                                            void* stream) {
+  if (!h || !bitstream) return MC_E_INVALID_ARG;
+  if (((uintptr_t)bitstream & 7) || ((uintptr_t)delta_out & 7) || ((uintptr_t)anchors_out & 7))
+    return MC_E_INVALID_ARG;
+  if (bytes < 64) return MC_E_BITSTREAM_CORRUPT;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  MC_TRY(cudaMemcpyAsync(h->h_header, bitstream, 64, cudaMemcpyDeviceToHost, s));
+  MC_TRY(cudaStreamSynchronize(s));
+  mesh_codec_status_t st = check_header(h, h->h_header, bytes);
+  if (st != MC_OK) return st;
+  const int n = h->n, F = h->F, k = h->k, W = h->W;
+  h->launches_decode = 0;
+  Launches L{&h->launches_decode};
+  cudaMemsetAsync(h->d_status, 0, sizeof(uint32_t), s);
+  unpack_sections(bitstream, h->lay, h->Udeq, h->Cdeq, h->Ahat, h->dec_anchors, nullptr,
+                  h->d_status, s, L);
+  if (delta_out) {
+    if (h->lp >= 0) {
+      mixed_backproject(h, s, L);
+    } else {
+      dgemm(n, F, k, 3, Strided{h->Cdeq, 1, n, (long long)k * n},
+            Strided{h->Udeq, 1, k, (long long)F * k}, StridedOut{h->D, W, 1, F}, 1, nullptr, s,
+            L);
+    }
+    MC_TRY(cudaMemcpyAsync(delta_out, h->D, sizeof(double) * n * W, cudaMemcpyDeviceToDevice, s));
+  }
+  if (anchors_out && h->n_c > 0)
+    MC_TRY(cudaMemcpyAsync(anchors_out, h->Ahat, sizeof(double) * 3 * h->n_c * F,
+                           cudaMemcpyDeviceToDevice, s));
+  MC_TRY(cudaGetLastError());
+  return read_status(h, s);
+}
+
+mesh_codec_status_t mesh_codec_set_start_basis(mesh_codec_t* h, const double* q0, void* stream) {
+  if (!h) return MC_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  Launches L{&h->launches_create};
+  MC_TRY(cudaMemsetAsync(h->d_status, 0, sizeof(uint32_t), s));
+  if (q0) {
+    MC_TRY(cudaMemcpyAsync(h->Q0, q0, sizeof(double) * 3 * h->F * h->k, cudaMemcpyDeviceToDevice,
+                           s));
+  } else {
+    gen_start_basis(h->Q0, h->F, h->k, h->p.seed, s, L);
+  }
+  const int sg = gemm_splits(h->F, ((h->k + 63) / 64) * ((h->k + 31) / 32));
+  cholqr3(h->Q0, h->F, h->k, h->G, h->Rf, h->partials, sg, h->d_status, s, L);
+  MC_TRY(cudaGetLastError());
+  return read_status(h, s);
 }
 
 static mesh_codec_status_t ensure_staging(mesh_codec* h) {

@@ -365,6 +365,69 @@ static void cg_init_t(const CgGeom& g, const double* B, void* X, void* R, void* 
   L.add(2);
 }
 
+// CG start from a given X (warm start): R = B - M X with Q = M X already
+// computed, P = D^-1 R, rz = R.(D^-1 R), bb = B.B (the stopping rule stays
+// relative to ||B||).
+template <typename T>
+__global__ void __launch_bounds__(kCgThreads) k_cg_init_warm(CgGeom g, const double* __restrict__ B,
+                                                             const T* __restrict__ Q,
+                                                             T* __restrict__ R, T* __restrict__ P,
+                                                             const T* __restrict__ inv_diag,
+                                                             double* __restrict__ partials) {
+  __shared__ double sh[256];
+  const int col = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int rl = threadIdx.x >> 5;
+  const bool valid = col < g.W;
+  const long long r0 = (long long)blockIdx.y * g.rows_per_block;
+  const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
+  DotAcc<T> rz;
+  DotAcc<double> bb;
+  if (valid) {
+    for (long long i = r0 + rl; i < r1; i += 8) {
+      const long long e = i * g.W + col;
+      const double b = B[e];
+      const T r = (T)(b - (double)Q[e]);
+      const T z = r * inv_diag[i];
+      R[e] = r;
+      P[e] = z;
+      rz.add(r, z);
+      bb.add(b, b);
+    }
+  }
+  const long long plane = (long long)g.row_blocks * g.W;
+  cta_col_partial(rz.value(), sh, partials, col, g.W, valid);
+  cta_col_partial(bb.value(), sh, partials + plane, col, g.W, valid);
+}
+
+template <typename T>
+static void cg_init_warm_t(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx,
+                           const int32_t* deg, const T* inv_d, const uint8_t* is_anchor, int kind,
+                           const double* B, T* X, T* R, T* P, T* Tv, T* Q, const T* inv_diag,
+                           CgState& st, cudaStream_t s, Launches& L) {
+  dim3 grid((g.W + 31) / 32, g.row_blocks);
+  cudaMemsetAsync(st.done, 0, sizeof(int32_t) * g.W, s);
+  k_cg_L<T><<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, X, Tv, st.done);
+  k_cg_LT<T><<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, is_anchor, Tv, X,
+                                          Q, st.done, st.partials);
+  k_cg_init_warm<T><<<grid, kCgThreads, 0, s>>>(g, B, Q, R, P, inv_diag, st.partials);
+  k_cg_init_cols<<<(g.W + 7) / 8, 256, 0, s>>>(g, st.partials, st.rz, st.bb, st.done, st.iters);
+  L.add(4);
+}
+
+void cg_init_warm(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx,
+                  const int32_t* deg, const void* inv_d, const uint8_t* is_anchor, int kind,
+                  const double* B, void* X, void* R, void* P, void* T, void* Q,
+                  const void* inv_diag, CgState& st, int single, cudaStream_t s, Launches& L) {
+  if (single)
+    cg_init_warm_t<float>(g, row_ptr, col_idx, deg, (const float*)inv_d, is_anchor, kind, B,
+                          (float*)X, (float*)R, (float*)P, (float*)T, (float*)Q,
+                          (const float*)inv_diag, st, s, L);
+  else
+    cg_init_warm_t<double>(g, row_ptr, col_idx, deg, (const double*)inv_d, is_anchor, kind, B,
+                           (double*)X, (double*)R, (double*)P, (double*)T, (double*)Q,
+                           (const double*)inv_diag, st, s, L);
+}
+
 void cg_init(const CgGeom& g, const double* B, void* X, void* R, void* P,
              const void* inv_diag, CgState& st, int single, cudaStream_t s, Launches& L) {
   if (cg4_applies(g.W, single)) {

@@ -192,6 +192,11 @@ void cg_iteration(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_id
                   double rtol, int max_iters, CgState& st, int single, cudaStream_t s,
                   Launches& L, cudaEvent_t* ev /* 7 events around the 6 kernels, or null */);
 void widen(const float* X, long long count, double* out, cudaStream_t s, Launches& L);
+// CG start from the X already in place (warm start), T and Q as scratch
+void cg_init_warm(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx,
+                  const int32_t* deg, const void* inv_d, const uint8_t* is_anchor, int kind,
+                  const double* B, void* X, void* R, void* P, void* T, void* Q,
+                  const void* inv_diag, CgState& st, int single, cudaStream_t s, Launches& L);
 // FP32 CG with four columns per thread (W % 4 == 0), mc_cg4.cu
 bool cg4_applies(int W, int single);
 void cg4_init(const CgGeom& g, const double* B, float* X, float* R, float* P,

@@ -54,6 +54,10 @@ class SequenceSpec:
     n_bumps: int = 0
     rigid: bool = True
     noise: float = 0.0
+    # temporal frequency multiplier (cycles per sequence are drawn in
+    # [0.5, 3] * tfreq); a sequence cut into S segments with tfreq = S gives
+    # every segment the temporal content of a standalone sequence
+    tfreq: float = 1.0
     extra: dict = field(default_factory=dict)
 
 
@@ -97,7 +101,7 @@ def sinusoid_rigid_motion(verts, spec, rng=None):
         wdir = _unit(rng, spec.n_fields)
         wmag = rng.uniform(1.0, 4.0, size=spec.n_fields)
         w = wdir * wmag[:, None]
-        fr = rng.uniform(0.5, 3.0, size=spec.n_fields)
+        fr = rng.uniform(0.5, 3.0, size=spec.n_fields) * spec.tfreq
         phi = rng.uniform(0.0, 2 * np.pi, size=spec.n_fields)
         psi = rng.uniform(0.0, 2 * np.pi, size=spec.n_fields)
         kappa = _unit(rng, spec.n_fields)
@@ -111,7 +115,7 @@ def sinusoid_rigid_motion(verts, spec, rng=None):
 
     if spec.bend:
         theta = np.arctan2(verts[:, 1], verts[:, 0])
-        wave = spec.bend * np.sin(2.0 * theta[None, :] - 2 * np.pi * t[:, None] / F)
+        wave = spec.bend * np.sin(2.0 * theta[None, :] - 2 * np.pi * spec.tfreq * t[:, None] / F)
         pos[:, :, 2] += wave
 
     if spec.n_bumps:
