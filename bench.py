@@ -8,7 +8,10 @@ sequence, with the input already resident in device memory.  The default
 workload is the 20 000-vertex torus sequence (F = 256 frames, k = 32,
 12-bit coefficients, 16-bit dictionary and anchors, 50 anchors) in the FP64
 mode; `--workload grid316_F512_k64 --precision tf32` measures the
-mixed-precision form on the 99 856-vertex grid sequence.
+mixed-precision form on the 99 856-vertex grid sequence, `--workload
+batched64 --precision tf32` 64 ragged sequences per step, and `--workload
+learned` the 262 144-vertex grid coded segment by segment with the learned
+warm starts against the plain ones.
 
 Prints ONE JSON line (rank 0).  Under torchrun each rank runs an independent
 replica on its own GPU (the codec does not shard a sequence); `value` is the
@@ -45,6 +48,11 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 CPU_SAMPLE_FRAMES = 64       # cpu_baseline: first 64 frames of the same sequence
 REF_SAMPLE_FRAMES = 32       # --impl reference: per-step sample
+LEARNED_OI_TOL = 1e-6        # learned workload: orthogonal iterations run to this change
+LEARNED_OI_CAP = 100
+LEARNED_FIELDS = 16          # learned workload motion: 16 fields,
+LEARNED_CYCLES = 8           # [0.5, 3] x 8 cycles per 300-frame segment
+LEARNED_CG_RTOL = 1e-8
 
 
 # ---------------------------------------------------------------- helpers
@@ -502,6 +510,180 @@ def run_batched(args):
     return 0
 
 
+def run_learned(args):
+    """The 512x512 grid (262,144 vertices, F = 300 per segment, k = 64, 2,621
+    anchors) as one coherent sequence coded segment by segment.  Each timed
+    step codes the next segment twice: once with the learned starts (start
+    basis of the FP64 orthogonal iterations to 1e-6; first iterate of the
+    FP32 CG), the online training of both networks included in the timed
+    region, and once with the plain starts (seeded basis, X0 = 0).  Two
+    untimed segments train the networks first."""
+    import torch
+
+    from oracle import metrics
+    from paper_2111_10105_gb300 import MeshCodec
+    from paper_2111_10105_gb300 import codec as cb
+    from paper_2111_10105_gb300.warm import WarmStart
+    from synth import config_spec
+    from synth.motion import base_mesh, sinusoid_rigid_motion
+
+    world, rank, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    base = config_spec("grid512_F300_k64")
+    F = base.n_frames
+    segs = 2 + args.warmup + args.steps
+    # richer motion than the standalone workload: 16 fields with 4-24 cycles
+    # per segment, so that rank 64 lies inside the numerical rank of every
+    # segment (sigma_64 / sigma_1 ~ 1e-3) and sweeps to a tolerance are defined
+    spec = config_spec("grid512_F300_k64", n_frames=F * segs, seed=base.seed + 100 * rank,
+                       n_fields=LEARNED_FIELDS, tfreq=LEARNED_CYCLES * segs)
+    cg_rtol = args.cg_rtol if args.cg_rtol is not None else LEARNED_CG_RTOL
+    verts, tris = base_mesh(spec.mesh)
+    n = verts.shape[0]
+    prec = PRECISION_CODE[args.precision if args.precision != "fp64" else "tf32"]
+    kw = dict(n_frames=F, rank=spec.rank, n_anchors=spec.n_anchors, seed=spec.seed,
+              coeff_bits=spec.coeff_bits, dict_bits=spec.dict_bits, anchor_bits=spec.anchor_bits,
+              solve_mode=0)
+    enc = MeshCodec(tris, n, oi_sweeps=LEARNED_OI_CAP, oi_tol=LEARNED_OI_TOL, **kw)
+    dec = MeshCodec(tris, n, precision=prec, oi_refine_sweeps=1, cg_rtol=cg_rtol, **kw)
+    ws = WarmStart(dec, torch.from_numpy(verts).to(dev), encoder=enc)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    bits = torch.empty(enc.stream_bytes, dtype=torch.uint8, device=dev)
+
+    def segment(s):
+        pos = sinusoid_rigid_motion(verts, spec, frame_range=(s * F, (s + 1) * F))
+        return pos, torch.from_numpy(pos).to(dev)
+
+    def timed(fn):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), out
+
+    phase_ms = {"encode": 0.0, "train_basis": 0.0, "predict_start": 0.0, "decode": 0.0,
+                "train_positions": 0.0}
+
+    def learned_step(pos_d, record=False):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        ev[0].record(stream)
+        enc.set_start_basis(ws.start_basis("learned"))
+        enc.encode(pos_d, out=bits)
+        sweeps = sum(enc.stats()["oi_sweeps"])
+        launches = enc.stats()["launches_encode"]
+        ev[1].record(stream)
+        ws.observe_basis(enc.buffer(cb.BUF_BASIS).view(3, F, spec.rank))
+        ev[2].record(stream)
+        x0, delta, anc = ws.initial_positions(bits, "learned")
+        ev[3].record(stream)
+        x = dec.decode(bits, x0=x0)
+        st = dec.stats()
+        ev[4].record(stream)
+        ws.observe_decoded(x, delta, anc)
+        ev[5].record(stream)
+        if record:
+            ev[5].synchronize()
+            for i, name in enumerate(phase_ms):
+                phase_ms[name] += ev[i].elapsed_time(ev[i + 1])
+        return x, sweeps, st["cg_iters_mean"], launches + st["launches_decode"]
+
+    def plain_step(pos_d):
+        enc.set_start_basis(None)
+        enc.encode(pos_d, out=bits)
+        sweeps = sum(enc.stats()["oi_sweeps"])
+        launches = enc.stats()["launches_encode"]
+        x = dec.decode(bits)
+        st = dec.stats()
+        return x, sweeps, st["cg_iters_mean"], launches + st["launches_decode"]
+
+    for s in range(2):                                    # training segments
+        _, pos_d = segment(s)
+        ws.encode(pos_d, start="previous", out=bits)
+        ws.decode(bits, start="previous")
+    for s in range(2, 2 + args.warmup):
+        _, pos_d = segment(s)
+        learned_step(pos_d)
+    sampler = ClockSampler()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    rows = []
+    ms_learned = ms_plain = 0.0
+    launches = 0
+    dec.set_profiling(16)
+    sampler.start()
+    for s in range(2 + args.warmup, segs):
+        pos, pos_d = segment(s)
+        # Algorithm 1's start (previous dictionary) and the previous-frame
+        # decoder start, untimed, for the comparison
+        enc.set_start_basis(ws.start_basis("previous"))
+        enc.encode(pos_d, out=bits)
+        prev_sweeps = sum(enc.stats()["oi_sweeps"])
+        x0, _, _ = ws.initial_positions(bits, "previous")
+        dec.decode(bits, x0=x0)
+        prev_iters = dec.stats()["cg_iters_mean"]
+        t_l, (x_l, sw_l, it_l, la) = timed(lambda: learned_step(pos_d, record=True))
+        launches += la
+        nm_l = metrics.nmse(pos, x_l.cpu().numpy())
+        t_p, (x_p, sw_p, it_p, _) = timed(lambda: plain_step(pos_d))
+        nm_p = metrics.nmse(pos, x_p.cpu().numpy())
+        ms_learned += t_l
+        ms_plain += t_p
+        rows.append({"segment": s, "ms_learned": round(t_l, 2), "ms_plain": round(t_p, 2),
+                     "oi_sweeps": {"seeded": sw_p, "previous": prev_sweeps, "learned": sw_l},
+                     "cg_iters_mean": {"cold": round(it_p, 1), "previous": round(prev_iters, 1),
+                                       "learned": round(it_l, 1)},
+                     "nmse": {"plain": nm_p, "learned": nm_l}})
+    clocks = sampler.stop()
+    profile = dec.profile()
+    dec.set_profiling(0)
+    stats = dec.stats()
+    vf = n * F * args.steps
+    value, seconds = aggregate(vf, ms_learned / 1e3, world, dist)
+    plain_value, _ = aggregate(vf, ms_plain / 1e3, world, dist)
+    nnz = int(dec.buffer(1).numel())
+    rl = roofline(profile, stats, n, stats["cg_columns"], nnz, spec.n_anchors, measured_peaks(),
+                  True)
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": seconds * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 encoder (OI to tolerance) + tf32/f32 decoder; bf16/f32 networks",
+            "data": "synthetic",
+            "config": {"workload": "learned", "mesh": spec.mesh, "n": n, "F": F, "k": spec.rank,
+                       "anchors": spec.n_anchors, "segments": segs,
+                       "oi_tol": LEARNED_OI_TOL, "oi_cap": LEARNED_OI_CAP, "cg_rtol": cg_rtol,
+                       "motion": f"{LEARNED_FIELDS} fields, "
+                                 f"{0.5 * LEARNED_CYCLES:g}-{3 * LEARNED_CYCLES:g} cycles "
+                                 "per segment, 4 bumps",
+                       "training": "online, 200 Adam steps x 65,536 rows per segment and network",
+                       "l2": "flushed (256 MiB write) before every timed region",
+                       "parallelism": f"replicas x{world}"},
+            "plain_value": plain_value, "speedup_vs_plain": value / plain_value,
+            "learned_phase_ms_per_step": {k: round(v / args.steps, 1) for k, v in phase_ms.items()},
+            "per_segment": rows, "roofline": rl, "clocks": clocks, "gpu_launches": launches,
+            "cpu_baseline": None, "e2e": None,
+        }
+        print(json.dumps(out), flush=True)
+    enc.close()
+    dec.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -511,6 +693,8 @@ def main(argv=None):
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--precision", choices=["fp64", "tf32", "bf16"], default="fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cg-rtol", type=float, default=None,
+                    help="decoder CG tolerance of the learned workload (default 1e-8)")
     ap.add_argument("--solve-mode", choices=["frames", "factored"], default="factored",
                     help="decoder right-hand sides: 3F frame columns (Eq. 11-12 as written) or "
                          "3k + n_c factored columns (same solution, reassociated)")
@@ -521,6 +705,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "batched64":
         return run_batched(args)
+    if args.workload == "learned":
+        return run_learned(args)
     return run_ours(args)
 
 

@@ -51,7 +51,10 @@ typedef enum mesh_codec_status {
     MC_E_NOT_CONVERGED = 6,      /* decoder solve hit its iteration cap; result written */
     MC_E_BITSTREAM_CORRUPT = 7,  /* header, sizes or anchor indices inconsistent */
     MC_E_BUFFER_TOO_SMALL = 8,   /* output capacity below the stream size; *written set */
-    MC_E_NUMERICAL = 9,          /* non-positive pivot in a Cholesky factor (rank-deficient data) */
+    MC_E_NUMERICAL = 9,          /* an orthonormal basis could not be formed (non-finite
+                                    input, or F above ~28,000 with rank-deficient data);
+                                    numerically rank-deficient trajectories are completed,
+                                    not rejected */
     MC_E_BAD_ANCHORS = 10        /* caller-supplied anchors not strictly increasing in [0, n) */
 } mesh_codec_status_t;
 
@@ -200,11 +203,12 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_decode_stage(mesh_codec_t* h, cons
                                                            double* anchors_out, void* stream);
 
 /* Start basis of the orthogonal iterations (Algorithm 1).  `q0`: device
- * float64 [3][F][k], made orthonormal (CholeskyQR3) and used by every
+ * float64 [3][F][k], made orthonormal (CholeskyQR3; columns dependent on
+ * earlier ones are replaced by seeded random directions) and used by every
  * following encode, e.g. the previous block's dictionary U[i-1] as
  * Algorithm 1 does for blocks 2..n_b; NULL restores the seeded random start.
- * Synchronises `stream`.  Errors: MC_E_INVALID_ARG, MC_E_NUMERICAL (rank-
- * deficient q0), MC_E_CUDA. */
+ * Synchronises `stream`.  Errors: MC_E_INVALID_ARG, MC_E_NUMERICAL
+ * (non-finite q0), MC_E_CUDA. */
 MESH_CODEC_API mesh_codec_status_t mesh_codec_set_start_basis(mesh_codec_t* h, const double* q0,
                                                               void* stream);
 
@@ -387,8 +391,9 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_mlp_get_params(const mesh_codec_ml
 MESH_CODEC_API mesh_codec_status_t mesh_codec_mlp_set_params(mesh_codec_mlp_t* m, const float* src,
                                                              void* stream);
 
-/* Y = network(X) for N rows, enqueued on `stream`.  Grows the handle's
- * activation buffers to N rows on first use of a larger N (cudaMalloc).
+/* Y = network(X) for N rows, enqueued on `stream`, in chunks of at most
+ * 4,194,304 rows.  Grows the handle's activation buffers to one chunk on
+ * first use of a larger N (cudaMalloc).
  * Errors: MC_E_INVALID_ARG, MC_E_OOM, MC_E_CUDA. */
 MESH_CODEC_API mesh_codec_status_t mesh_codec_mlp_forward(mesh_codec_mlp_t* m, const float* X,
                                                           long long N, float* Y, void* stream);

@@ -61,6 +61,8 @@ size_t carve(mesh_codec* h, void* base) {
   h->H = c.take<double>(3 * k * k);
   h->G = c.take<double>(3 * k * k);
   h->Rf = c.take<double>(3 * k * k);
+  h->qr_save = c.take<double>(3 * F * k);
+  h->qr_bad = c.take<uint32_t>(4);
   h->theta = c.take<double>(3 * k);
   h->Wk = c.take<double>(3 * n * k);
   h->partials = c.take<double>(h->partial_elems);
@@ -170,7 +172,7 @@ const char* mesh_codec_status_string(mesh_codec_status_t s) {
     case MC_E_NOT_CONVERGED: return "decoder solve did not converge";
     case MC_E_BITSTREAM_CORRUPT: return "corrupt bitstream";
     case MC_E_BUFFER_TOO_SMALL: return "output buffer too small";
-    case MC_E_NUMERICAL: return "numerical breakdown (rank-deficient trajectories)";
+    case MC_E_NUMERICAL: return "no orthonormal basis (non-finite data)";
     case MC_E_BAD_ANCHORS: return "bad anchor indices";
   }
   return "unknown status";
@@ -301,7 +303,7 @@ static mesh_codec_status_t create_impl(mesh_codec* h, const int32_t* tris_in, in
   // starting basis Q0: splitmix64 uniforms made orthonormal by CholeskyQR3
   gen_start_basis(h->Q0, h->F, h->k, h->p.seed, s, L);
   int sg = gemm_splits(h->F, ((h->k + 63) / 64) * ((h->k + 31) / 32));
-  cholqr3(h->Q0, h->F, h->k, h->G, h->Rf, h->partials, sg, h->d_status, s, L);
+  cholqr3(h->Q0, h->F, h->k, qr_work(h, sg), nullptr, h->d_status, s, L);
   mesh_codec_status_t st = read_status(h, s);
   int32_t nnz = 0;
   if (st == MC_OK) {
@@ -377,7 +379,7 @@ static void enqueue_encode(mesh_codec* h, const double* positions, uint8_t* out,
           StridedOut{h->Wk, k, 1, (long long)n * k}, 1, nullptr, s, L);
     dgemm(F, k, n, 3, XcT, Strided{h->Wk, k, 1, (long long)n * k},
           StridedOut{h->Zb, k, 1, (long long)F * k}, sz, h->partials, s, L);
-    cholqr3(h->Zb, F, k, h->G, h->Rf, h->partials, sg, h->d_status, s, L);
+    cholqr3(h->Zb, F, k, qr_work(h, sg), h->Q, h->d_status, s, L);
     for (int c = 0; c < 3; ++c) h->oi_done[c] = t + 1;
     bool stop = false;
     if (host_check_tol && h->p.oi_tol > 0.0) {
@@ -748,7 +750,7 @@ mesh_codec_status_t mesh_codec_set_start_basis(mesh_codec_t* h, const double* q0
     gen_start_basis(h->Q0, h->F, h->k, h->p.seed, s, L);
   }
   const int sg = gemm_splits(h->F, ((h->k + 63) / 64) * ((h->k + 31) / 32));
-  cholqr3(h->Q0, h->F, h->k, h->G, h->Rf, h->partials, sg, h->d_status, s, L);
+  cholqr3(h->Q0, h->F, h->k, qr_work(h, sg), nullptr, h->d_status, s, L);
   MC_TRY(cudaGetLastError());
   return read_status(h, s);
 }

@@ -149,9 +149,11 @@ void gen_start_basis(double* Z, int F, int k, uint64_t seed, cudaStream_t s, Lau
 // R = chol(G) upper triangular with positive diagonal (one CTA per
 // coordinate), Z <- Z R^-1 (rows in parallel).  The product of the three R
 // factors has a positive diagonal, so the result is the unique thin-QR Q.
+// A non-positive pivot marks the coordinate in bad[c] (the fallback below
+// then recomputes its Q) and leaves R = I, so the pass keeps Z unchanged.
 __global__ void __launch_bounds__(1024) k_cholesky(const double* __restrict__ G,
                                                    double* __restrict__ R, int k, int F,
-                                                   int shifted, uint32_t* status) {
+                                                   int shifted, uint32_t* bad) {
   extern __shared__ double A[];  // k x k
   const int c = blockIdx.x;
   const double* Gc = G + (long long)c * k * k;
@@ -169,13 +171,13 @@ __global__ void __launch_bounds__(1024) k_cholesky(const double* __restrict__ G,
     for (int i = threadIdx.x; i < k; i += blockDim.x) A[i * k + i] += sh;
     __syncthreads();
   }
-  __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
+  __shared__ int bad_pivot;
+  if (threadIdx.x == 0) bad_pivot = 0;
   __syncthreads();
   for (int j = 0; j < k; ++j) {
     double piv = A[j * k + j];
     if (!(piv > 0.0)) {
-      if (threadIdx.x == 0) bad = 1;
+      if (threadIdx.x == 0) bad_pivot = 1;
       break;
     }
     double rjj = sqrt(piv);
@@ -193,8 +195,8 @@ __global__ void __launch_bounds__(1024) k_cholesky(const double* __restrict__ G,
     __syncthreads();
   }
   __syncthreads();
-  if (bad) {
-    if (threadIdx.x == 0) atomicOr(status, ST_CHOL_BREAKDOWN);
+  if (bad_pivot) {
+    if (threadIdx.x == 0) bad[c] = 1;
     for (int e = threadIdx.x; e < k * k; e += blockDim.x) Rc[e] = (e / k == e % k) ? 1.0 : 0.0;
     return;
   }
@@ -226,19 +228,171 @@ __global__ void __launch_bounds__(64) k_trsm_rows(double* __restrict__ Z,
   for (int j = 0; j < k; ++j) z[j] = q[j];
 }
 
-void cholqr3(double* Z, int F, int k, double* G, double* R, double* partials, int splits,
-             uint32_t* status, cudaStream_t s, Launches& L) {
+// bad[c] |= Q_c^T Q_c differs from I by more than 1e-10 anywhere (or is not
+// finite): CholeskyQR3 kept every pivot positive but Z was too ill-conditioned
+// for it (condition number near 1 / unit roundoff).
+__global__ void k_orth_check(const double* __restrict__ G, int k, uint32_t* bad) {
+  const int c = blockIdx.x;
+  const double* Gc = G + (long long)c * k * k;
+  int off = 0;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const double d = Gc[e] - ((e / k == e % k) ? 1.0 : 0.0);
+    if (!(fabs(d) <= 1e-10)) off = 1;
+  }
+  if (__syncthreads_or(off) && threadIdx.x == 0) bad[c] = 1;
+}
+
+// Fallback thin QR for the coordinates flagged in bad[]: one CTA per
+// coordinate recomputes Q from the saved Z by classical Gram-Schmidt with
+// reorthogonalisation (a second pass, and a third while a pass still removes
+// more than half the norm: Giraud, Langou, Rozloznik, "The loss of
+// orthogonality in the Gram-Schmidt orthogonalization process", Comput.
+// Math. Appl. 2005).  A column left with at most 1e-9 of its norm is
+// numerically dependent on the earlier ones and is replaced, in this order,
+// by the fill column j (the previous iterate, which keeps a completed basis
+// stable from sweep to sweep) and by seeded uniform vectors (splitmix64 of
+// seed ^ (kCompleteSalt + c), element (attempt * k + j) * F + f).  Full-rank
+// columns give the thin-QR Q with a positive diagonal of R, as CholeskyQR3.
+constexpr int kQrThreads = 256;
+
+__device__ double qr_block_sum(double x, double* red) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = x;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < kQrThreads / 32; ++w) s += red[w];
+  return s;
+}
+
+__global__ void __launch_bounds__(kQrThreads) k_qr_robust(double* __restrict__ Z,
+                                                          const double* __restrict__ save,
+                                                          const double* __restrict__ fill, int F,
+                                                          int k, const uint32_t* __restrict__ bad,
+                                                          uint64_t seed, uint32_t* status) {
+  const int c = blockIdx.x;
+  if (!bad[c]) return;
+  extern __shared__ double sm[];
+  double* v = sm;                                    // [F] the column being built
+  double* r = v + F;                                 // [k] projection coefficients
+  double* red = r + MESH_CODEC_MAX_RANK;             // [(threads / 32) * k] partial sums
+  double* Q = Z + (long long)c * F * k;
+  const double* S = save + (long long)c * F * k;
+  const double* Fl = fill ? fill + (long long)c * F * k : nullptr;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int j = 0; j < k; ++j) {
+    bool done = false;
+    for (int attempt = 0; attempt < 5 && !done; ++attempt) {
+      for (int f = tid; f < F; f += kQrThreads) {
+        double x;
+        if (attempt == 0) {
+          x = S[(long long)f * k + j];
+        } else if (attempt == 1 && Fl) {
+          x = Fl[(long long)f * k + j];
+        } else {
+          const uint64_t u = splitmix64_at(seed ^ (kCompleteSalt + (uint64_t)c),
+                                           ((uint64_t)attempt * k + j) * F + f) >> 11;
+          x = (double)u * 0x1.0p-53 * 2.0 - 1.0;
+        }
+        v[f] = x;
+      }
+      __syncthreads();
+      double part = 0.0;
+      for (int f = tid; f < F; f += kQrThreads) part += v[f] * v[f];
+      const double n0 = sqrt(qr_block_sum(part, red));
+      if (!(n0 > 0.0) || !isfinite(n0)) continue;
+      double nv = n0;
+      for (int pass = 0; pass < 3 && j > 0; ++pass) {
+        // r_i = q_i . v for i < j: per-thread partials, then warp and block sums
+        double acc[MESH_CODEC_MAX_RANK];
+#pragma unroll
+        for (int i = 0; i < MESH_CODEC_MAX_RANK; ++i) acc[i] = 0.0;
+        for (int f = tid; f < F; f += kQrThreads) {
+          const double vf = v[f];
+          const double* qrow = Q + (long long)f * k;
+#pragma unroll
+          for (int i = 0; i < MESH_CODEC_MAX_RANK; ++i)
+            if (i < j) acc[i] = fma(qrow[i], vf, acc[i]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < MESH_CODEC_MAX_RANK; ++i) {
+          if (i < j) {
+            double x = acc[i];
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) red[warp * MESH_CODEC_MAX_RANK + i] = x;
+          }
+        }
+        __syncthreads();
+        for (int i = tid; i < j; i += kQrThreads) {
+          double x = 0.0;
+          for (int w = 0; w < kQrThreads / 32; ++w) x += red[w * MESH_CODEC_MAX_RANK + i];
+          r[i] = x;
+        }
+        __syncthreads();
+        part = 0.0;
+        for (int f = tid; f < F; f += kQrThreads) {
+          const double* qrow = Q + (long long)f * k;
+          double x = v[f];
+          for (int i = 0; i < j; ++i) x = fma(-r[i], qrow[i], x);
+          v[f] = x;
+          part += x * x;
+        }
+        const double nn = sqrt(qr_block_sum(part, red));
+        const bool enough = !(nn < 0.5 * nv);
+        nv = nn;
+        if (enough) break;
+      }
+      if (nv > 1e-9 * n0 && isfinite(nv)) {
+        const double inv = 1.0 / nv;
+        for (int f = tid; f < F; f += kQrThreads) Q[(long long)f * k + j] = v[f] * inv;
+        done = true;
+      }
+      __syncthreads();
+    }
+    if (!done) {
+      if (tid == 0) atomicOr(status, ST_CHOL_BREAKDOWN);
+      return;
+    }
+  }
+}
+
+__global__ void k_flag_bad(const uint32_t* bad, uint32_t* status) {
+  if (threadIdx.x < 3 && bad[threadIdx.x]) atomicOr(status, ST_CHOL_BREAKDOWN);
+}
+
+void cholqr3(double* Z, int F, int k, const QrWork& w, const double* fill, uint32_t* status,
+             cudaStream_t s, Launches& L) {
+  cudaMemcpyAsync(w.save, Z, sizeof(double) * 3 * F * k, cudaMemcpyDeviceToDevice, s);
+  cudaMemsetAsync(w.bad, 0, sizeof(uint32_t) * 3, s);
+  Strided A{Z, 1, k, (long long)F * k};
+  Strided B{Z, k, 1, (long long)F * k};
+  StridedOut C{w.G, k, 1, (long long)k * k};
   for (int pass = 0; pass < 3; ++pass) {
     // G_c = Z_c^T Z_c : (k x F)(F x k)
-    Strided A{Z, 1, k, (long long)F * k};
-    Strided B{Z, k, 1, (long long)F * k};
-    StridedOut C{G, k, 1, (long long)k * k};
-    dgemm(k, k, F, 3, A, B, C, splits, partials, s, L);
-    k_cholesky<<<3, 256, sizeof(double) * k * k, s>>>(G, R, k, F, pass == 0, status);
+    dgemm(k, k, F, 3, A, B, C, w.splits, w.partials, s, L);
+    k_cholesky<<<3, 256, sizeof(double) * k * k, s>>>(w.G, w.R, k, F, pass == 0, w.bad);
     dim3 g((F + 63) / 64, 3);
-    k_trsm_rows<<<g, 64, sizeof(double) * k * k, s>>>(Z, R, F, k);
+    k_trsm_rows<<<g, 64, sizeof(double) * k * k, s>>>(Z, w.R, F, k);
     L.add(2);
   }
+  // orthogonality of the result, then the fallback where it failed
+  dgemm(k, k, F, 3, A, B, C, w.splits, w.partials, s, L);
+  k_orth_check<<<3, 256, 0, s>>>(w.G, k, w.bad);
+  const size_t smem = sizeof(double) * (F + MESH_CODEC_MAX_RANK +
+                                        (kQrThreads / 32) * MESH_CODEC_MAX_RANK);
+  if (smem > 227 * 1024) {
+    // the column does not fit in shared memory (F above ~28,000 frames): a
+    // flagged coordinate is reported instead of repaired
+    k_flag_bad<<<1, 32, 0, s>>>(w.bad, status);
+  } else {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_qr_robust, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_qr_robust<<<3, kQrThreads, smem, s>>>(Z, w.save, fill, F, k, w.bad, w.seed, status);
+  }
+  L.add(2);
 }
 
 // ||Q_new - Q_old (Q_old^T Q_new)||_F per coordinate; P = Q_old (Q_old^T Q_new)

@@ -29,6 +29,8 @@ struct mesh_codec {
   float *inv_d32, *inv_diag32;     // FP32 copies for the mixed-precision CG
   double *Q0, *Q, *Zb, *U, *V, *H, *theta, *Wk, *partials, *chg_work, *chg;
   double *G, *Rf;
+  double* qr_save;                 // the orthonormalisation's saved input [3][F][k]
+  uint32_t* qr_bad;                // its per-coordinate fallback flags
   double *Cf, *qparams;
   double *X, *D, *B, *R, *P, *Tv, *Qv;
   double *Udeq, *Cdeq, *Ahat;
@@ -79,6 +81,10 @@ struct mesh_codec {
 };
 
 namespace mc {
+// the handle's orthonormalisation workspace, split-K over `splits`
+inline QrWork qr_work(mesh_codec* h, int splits) {
+  return QrWork{h->G, h->Rf, h->partials, h->qr_save, h->qr_bad, splits, h->p.seed};
+}
 // mixed-precision helpers (mc_mixed.cu)
 void mixed_dims(mesh_codec* h);
 size_t mixed_carve(mesh_codec* h, char* base, size_t off);

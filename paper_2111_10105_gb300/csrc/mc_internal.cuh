@@ -40,6 +40,8 @@ __host__ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t s, uint64_t 
 // The codec's salts: part of its definition ("anchors!", "basis_00").
 constexpr uint64_t kAnchorSalt = 0x616E63686F727321ull;
 constexpr uint64_t kBasisSalt = 0x62617369735F3030ull;
+// completion of a numerically rank-deficient basis ("complete")
+constexpr uint64_t kCompleteSalt = 0x636F6D706C657465ull;
 
 struct Launches {
   uint64_t* counter = nullptr;
@@ -99,9 +101,20 @@ struct StridedOut {
 void dgemm(int M, int N, int K, int batch, Strided A, Strided B, StridedOut C, int splits,
            double* partials, cudaStream_t s, Launches& L);
 void gen_start_basis(double* Z, int F, int k, uint64_t seed, cudaStream_t s, Launches& L);
-// Q = qr(Z) by shifted CholeskyQR3, batch of 3, in place on Z (Z -> Q)
-void cholqr3(double* Z, int F, int k, double* G, double* R, double* partials, int splits,
-             uint32_t* status, cudaStream_t s, Launches& L);
+// Q = qr(Z) by shifted CholeskyQR3, batch of 3, in place on Z (Z -> Q).
+// Workspace of the orthonormalisation: Gram and factor [3][k][k], split-K
+// partials, a copy of the input [3][F][k] and one flag per coordinate.
+struct QrWork {
+  double *G, *R, *partials, *save;
+  uint32_t* bad;
+  int splits;
+  uint64_t seed;
+};
+// Z [3][F][k] <- its thin-QR factor Q.  `fill` ([3][F][k], e.g. the previous
+// iterate, or null for seeded random vectors) completes the basis where Z is
+// numerically rank deficient.
+void cholqr3(double* Z, int F, int k, const QrWork& w, const double* fill, uint32_t* status,
+             cudaStream_t s, Launches& L);
 void oi_change(const double* Qold, const double* Qnew, int F, int k, double* work,
                double* change, cudaStream_t s, Launches& L);
 // eigen-decomposition of H (3 x k x k): V (k x k, columns = eigenvectors,

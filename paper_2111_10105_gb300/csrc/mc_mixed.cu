@@ -128,7 +128,7 @@ void mixed_oi_sweeps(mesh_codec* h, int sweeps, cudaStream_t s, Launches& L) {
     k_crop<<<(int)std::min<long long>((3 * F * k + 255) / 256, 1024), 256, 0, s>>>(
         h->Zfull, (int)F, (int)k, (int)Fp, (int)kp, h->Zb);
     L.add(1);
-    cholqr3(h->Zb, (int)F, (int)k, h->G, h->Rf, h->partials, sg, h->d_status, s, L);
+    cholqr3(h->Zb, (int)F, (int)k, qr_work(h, sg), h->Q, h->d_status, s, L);
     std::swap(h->Q, h->Zb);
     if (t + 1 < sweeps) pack_Qt(h, h->Q, h->Qtlp, s, L);
   }

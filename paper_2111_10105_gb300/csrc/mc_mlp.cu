@@ -41,6 +41,9 @@ struct mesh_codec_mlp {
 
 namespace {
 
+// rows per chunk of an inference call (activations: 4 x n_hidden floats per row)
+constexpr long long kForwardChunk = 1LL << 22;
+
 // ---------------------------------------------------------------- SIMT GEMM
 // C(m, n) = sum_k A(m, k) B(k, n) in FP32, A and B float or bf16, strided;
 // split-K partials summed in a fixed order by k_sum_partials_f.
@@ -62,7 +65,8 @@ __global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const TA* __
   __shared__ float As[TK][TM + 1];
   __shared__ float Bs[TK][TN + 1];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  // row tiles on x (up to 2^31 - 1 of them), column tiles on y (n <= 4096)
+  const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
   const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
   float acc[4][4] = {};
   for (int k0 = kb; k0 < ke; k0 += TK) {
@@ -133,7 +137,7 @@ void sgemm(mesh_codec_mlp* m, int M, int N, int K, const TA* A, long long as0, l
   int kchunk = (K + splits - 1) / splits;
   kchunk = (kchunk + TK - 1) / TK * TK;
   splits = (K + kchunk - 1) / kchunk;
-  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, splits);
+  dim3 grid((M + TM - 1) / TM, (N + TN - 1) / TN, splits);
   k_sgemm<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, as0, as1, B, bs0, bs1,
                                        splits == 1 ? C : m->part, cs0, cs1, kchunk);
   if (splits > 1) {
@@ -589,9 +593,12 @@ mesh_codec_status_t mesh_codec_mlp_set_params(mesh_codec_mlp_t* m, const float* 
 mesh_codec_status_t mesh_codec_mlp_forward(mesh_codec_mlp_t* m, const float* X, long long N,
                                            float* Y, void* stream) {
   if (!m || !X || !Y || N < 1) return MC_E_INVALID_ARG;
-  mesh_codec_status_t st = ensure_batch(m, (size_t)N);
+  // inference over many rows runs in chunks, so the activations stay small
+  const long long chunk = std::min<long long>(N, kForwardChunk);
+  mesh_codec_status_t st = ensure_batch(m, (size_t)chunk);
   if (st != MC_OK) return st;
-  forward(m, X, N, Y, (cudaStream_t)stream);
+  for (long long r = 0; r < N; r += chunk)
+    forward(m, X + r * m->nin, std::min(chunk, N - r), Y + r * m->nout, (cudaStream_t)stream);
   return cudaGetLastError() == cudaSuccess ? MC_OK : MC_E_CUDA;
 }
 

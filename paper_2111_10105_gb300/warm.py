@@ -52,14 +52,17 @@ class _Trainer:
 
 
 class WarmStart:
-    """Online warm starts for one codec handle (frames solve mode).
+    """Online warm starts for one codec handle (frames solve mode), or for
+    a decoder handle plus an encoder handle of the same connectivity,
+    anchors and sizes (e.g. an FP64 encoder and a mixed-precision decoder).
 
     rest: CUDA float64 [n, 3], the rest pose used for the anchor distances.
     """
 
     def __init__(self, codec, rest, hidden=256, seed=1, lr=1e-3, steps=200, batch=65536,
-                 basis_steps=200):
+                 basis_steps=200, encoder=None):
         self.codec = codec
+        self.enc = encoder if encoder is not None else codec
         self.n, self.F, self.k = codec.n, codec.F, codec.k
         self.anchors = codec.buffer(_c.BUF_ANCHORS)
         self.nearest, self.dist = _c.nearest_anchors(rest.contiguous(), self.anchors)
@@ -122,9 +125,9 @@ class WarmStart:
             self.basis.fit(feat, tgt)
         self.U_prev = U.clone()
 
-    def encode(self, positions, start="learned", learn=True):
-        self.codec.set_start_basis(self.start_basis(start))
-        bs = self.codec.encode(positions)
+    def encode(self, positions, start="learned", learn=True, out=None):
+        self.enc.set_start_basis(self.start_basis(start))
+        bs = self.enc.encode(positions, out=out)
         if learn:
-            self.observe_basis(self.codec.buffer(_c.BUF_BASIS).view(3, self.F, self.k))
+            self.observe_basis(self.enc.buffer(_c.BUF_BASIS).view(3, self.F, self.k))
         return bs

@@ -84,17 +84,24 @@ def _rotation(axis, angle):
     return np.eye(3) + math.sin(angle) * K + (1.0 - math.cos(angle)) * (K @ K)
 
 
-def sinusoid_rigid_motion(verts, spec, rng=None):
+def sinusoid_rigid_motion(verts, spec, rng=None, frame_range=None):
     """Apply the motion model of ``spec`` to base vertices ``verts``.
 
-    Returns float64 [F, n, 3].
+    Returns float64 [F, n, 3], or only frames f0 .. f1-1 of the same
+    sequence for ``frame_range = (f0, f1)`` (identical values; the random
+    parameters are drawn the same way; not with noise, whose draw depends
+    on the number of frames).
     """
     if rng is None:
         rng = np.random.default_rng(spec.seed)
     F = spec.n_frames
     n = verts.shape[0]
-    t = np.arange(F, dtype=np.float64)
-    pos = np.broadcast_to(verts, (F, n, 3)).copy()
+    f0, f1 = (0, F) if frame_range is None else frame_range
+    if frame_range is not None and spec.noise:
+        raise ValueError("frame_range with noise")
+    t = np.arange(f0, f1, dtype=np.float64)
+    Fr = f1 - f0
+    pos = np.broadcast_to(verts, (Fr, n, 3)).copy()
 
     if spec.n_fields:
         d = _unit(rng, spec.n_fields)
@@ -126,7 +133,7 @@ def sinusoid_rigid_motion(verts, spec, rng=None):
         lam = t / max(F - 1, 1)
         for b in range(spec.n_bumps):
             c = c0[b][None, :] + lam[:, None] * (c1[b] - c0[b])[None, :]   # [F,2]
-            for f in range(F):
+            for f in range(Fr):
                 r2 = ((verts[:, :2] - c[f]) ** 2).sum(1)
                 pos[f, :, 2] += h[b] * np.exp(-r2 / (2 * s[b] ** 2))
 
@@ -135,7 +142,7 @@ def sinusoid_rigid_motion(verts, spec, rng=None):
         ang_max = rng.uniform(0.0, np.pi / 4)
         tr_max = rng.uniform(0.0, 0.5, size=3)
         lam = t / max(F - 1, 1)
-        for f in range(F):
+        for f in range(Fr):
             Rf = _rotation(axis, ang_max * lam[f])
             pos[f] = pos[f] @ Rf.T + lam[f] * tr_max[None, :]
 
