@@ -23,6 +23,11 @@ steps in order:
 * ``codec``    - encoder (Eq. 7-10) and decoder (anchored least squares,
                  Eq. 12), with the bitstream layout.
 * ``metrics``  - NMSE and the bit-rate accounting of Eq. 13.
+* ``blocks``   - the blocks variant (Section III-A, Algorithm 1 across
+                 blocks) with the difference coding of consecutive
+                 dictionaries (Section IV, Fig. 6).
+* ``mlp``, ``warm`` - the learned warm start (not in the paper): the
+                 perceptron in FP64 and its input features.
 
 Parity status per function is stated in each module header; functions whose
 output no pin fixes say "parity unpinned" there.

@@ -115,20 +115,26 @@ def _encode_section(values, lo, hi, bits):
     return w + b"\0" * (_pad8(len(w)) - len(w))
 
 
-def encode(tris, positions, p, return_info=False):
+def encode(tris, positions, p, return_info=False, basis=None, dict_ref=None, dict_bits=None):
+    """Encodes one block.  `basis` (three F x k matrices) replaces the
+    orthogonal iterations from the seeded start (the blocks variant, Section
+    III-A, supplies its own U[i]); with `dict_ref` (three F x k matrices) the
+    dictionary section carries U - dict_ref (the difference coding of
+    consecutive dictionaries, Section IV, Fig. 6) in `dict_bits` bits."""
     positions = np.asarray(positions, dtype=np.float64)
     F, n, three = positions.shape
     assert three == 3 and F == p.n_frames
     k = p.rank
     if not (1 <= k <= F):
         raise ValueError("rank must satisfy 1 <= k <= F")
+    db = p.dict_bits if dict_bits is None else dict_bits
     row_ptr, col_idx, deg = graph.build_adjacency(tris, n)
     anchors = select_anchors(n, p.n_anchors, p.seed)
 
     header = bytearray(HEADER_BYTES)
-    total = stream_size(n, F, k, p.n_anchors, p.coeff_bits, p.dict_bits, p.anchor_bits)
+    total = stream_size(n, F, k, p.n_anchors, p.coeff_bits, db, p.anchor_bits)
     struct.pack_into("<4sIIIIIBBBBIQ", header, 0, MAGIC, VERSION, n, F, k,
-                     p.n_anchors, p.coeff_bits, p.dict_bits, p.anchor_bits,
+                     p.n_anchors, p.coeff_bits, db, p.anchor_bits,
                      p.laplacian_kind, HEADER_BYTES, total)
     out = [bytes(header)]
     a = anchors.astype("<i4").tobytes()
@@ -138,18 +144,23 @@ def encode(tris, positions, p, return_info=False):
             "anchors": anchors, "csr": (row_ptr, col_idx, deg)}
     for c in range(3):
         A_c = positions[:, :, c]                                    # F x n
-        U, theta, done, change = subspace.top_k_basis(A_c, k, p.seed, c, p.oi_sweeps, p.oi_tol)
+        if basis is None:
+            U, theta, done, change = subspace.top_k_basis(A_c, k, p.seed, c, p.oi_sweeps,
+                                                          p.oi_tol)
+        else:
+            U, theta, done, change = basis[c], None, 0, 0.0
         delta = graph.apply_laplacian(row_ptr, col_idx, deg, A_c.T, p.laplacian_kind)  # n x F
         C = U.T @ delta.T                                            # k x n
         anc_vals = A_c[:, anchors].T                                 # n_c x F
-        d_lo, d_hi = quant.quant_params(U, axis=0)
+        Ud = U if dict_ref is None else U - dict_ref[c]             # coded dictionary
+        d_lo, d_hi = quant.quant_params(Ud, axis=0)
         c_lo, c_hi = quant.quant_params(C, axis=1)
         if anchors.shape[0]:
             a_lo, a_hi = quant.quant_params(anc_vals)
         else:
             a_lo, a_hi = np.float64(0.0), np.float64(0.0)
         out.append(np.concatenate([d_lo, d_hi, c_lo, c_hi, [a_lo, a_hi]]).astype("<f8").tobytes())
-        out.append(_encode_section(U.T, d_lo[:, None], d_hi[:, None], p.dict_bits))
+        out.append(_encode_section(Ud.T, d_lo[:, None], d_hi[:, None], db))
         out.append(_encode_section(C, c_lo[:, None], c_hi[:, None], p.coeff_bits))
         out.append(_encode_section(anc_vals, a_lo, a_hi, p.anchor_bits))
         for key, v in (("U", U), ("theta", theta), ("C", C), ("delta", delta),
@@ -164,8 +175,10 @@ class BitstreamError(ValueError):
     pass
 
 
-def parse(blob):
-    """Bitstream -> dict of dequantized pieces (per coordinate lists)."""
+def parse(blob, dict_ref=None):
+    """Bitstream -> dict of dequantized pieces (per coordinate lists); with
+    `dict_ref` the dictionary section holds differences and dict_ref is added
+    back."""
     if len(blob) < HEADER_BYTES:
         raise BitstreamError("truncated header")
     (magic, version, n, F, k, n_c, cb, db, ab, kind, hb, total) = struct.unpack_from(
@@ -205,7 +218,7 @@ def parse(blob):
         Ut = section(F * k, db, np.repeat(d_lo, F), np.repeat(d_hi, F)).reshape(k, F)
         C = section(k * n, cb, np.repeat(c_lo, n), np.repeat(c_hi, n)).reshape(k, n)
         A = section(n_c * F, ab, a_lo, a_hi).reshape(n_c, F)
-        res["U"].append(Ut.T)
+        res["U"].append(Ut.T if dict_ref is None else Ut.T + dict_ref[c])
         res["C"].append(C)
         res["a"].append(A)
     assert off == total
@@ -281,8 +294,8 @@ def solve_anchored_ls(row_ptr, col_idx, deg, anchors, delta_t, a_hat, kind=0):
     return X, b, M
 
 
-def decode(blob, tris):
-    d = parse(blob)
+def decode(blob, tris, dict_ref=None):
+    d = parse(blob, dict_ref)
     n, F = d["n"], d["F"]
     row_ptr, col_idx, deg = graph.build_adjacency(tris, n)
     out = np.empty((F, n, 3), dtype=np.float64)
