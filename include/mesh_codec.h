@@ -99,7 +99,12 @@ typedef struct mesh_codec_params {
     int32_t autotune;            /* 1: time candidate CG tile shapes on the first decode of each
                                     column count and keep the fastest (results then depend on
                                     the chosen shape at rounding level); 0: fixed shape */
-    int32_t reserved[5];         /* must be zero */
+    int32_t block_delta;         /* blocks variant (mesh_codec_encode_blocks): 1 = blocks
+                                    2..n_b code their dictionary as the difference from
+                                    the decoder's previous dictionary (Section IV, Fig. 6);
+                                    0 = every block codes its own dictionary */
+    int32_t block_delta_bits;    /* bits per dictionary difference, 0..31 (0 = raw binary64) */
+    int32_t reserved[3];         /* must be zero */
 } mesh_codec_params_t;
 
 typedef struct mesh_codec_stats {
@@ -211,6 +216,44 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_decode_stage(mesh_codec_t* h, cons
  * (non-finite q0), MC_E_CUDA. */
 MESH_CODEC_API mesh_codec_status_t mesh_codec_set_start_basis(mesh_codec_t* h, const double* q0,
                                                               void* stream);
+
+/* Blocks variant (Section III-A, Algorithm 1).  A sequence of
+ * n_blocks * F frames (F = the handle's n_frames, the paper's k_f) is coded
+ * as n_blocks consecutive blocks with the handle's connectivity, anchors and
+ * parameters:
+ *   block 1: U[1] from the eigendecomposition of R[1] = A A^T (Algorithm 1's
+ *            SVD; F <= 64; for F > 64 the seeded one-block iterations);
+ *   block i >= 2: oi_sweeps sweeps Q <- QR(R[i] Q) from Q = U[i-1]
+ *            (Algorithm 1), then Rayleigh-Ritz and signs as for one block;
+ *   with params.block_delta, blocks i >= 2 code U[i] - U^[i-1] (U^ the
+ *            dequantized dictionary the decoder holds) in block_delta_bits.
+ * Container: 64-byte header (magic "DMCB", u32 version 1, u32 n_blocks,
+ * u32 flags (bit 0: differences), u32 delta bits, u64 first block bytes,
+ * u64 other block bytes, u64 total bytes, zero padding), then the block
+ * streams in order, each a version-1 stream of mesh_codec_encode.
+ * mesh_codec_blocks_size gives the container size for n_blocks. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_blocks_size(const mesh_codec_t* h, int n_blocks,
+                                                          size_t* bytes);
+
+/* positions: device float64 [n_blocks * F][n][3]; out: device, 8-byte
+ * aligned, `capacity` bytes; *written = the container size (also on
+ * MC_E_BUFFER_TOO_SMALL).  Leaves the handle's start basis unchanged.
+ * Synchronises `stream` at the end.  Errors: as mesh_codec_encode. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_encode_blocks(mesh_codec_t* h,
+                                                            const double* positions,
+                                                            int n_blocks, uint8_t* out,
+                                                            size_t capacity, size_t* written,
+                                                            void* stream);
+
+/* Decodes a container of mesh_codec_encode_blocks into positions_out
+ * (device float64 [n_blocks * F][n][3], n_blocks from the container).  In
+ * the frames solve mode each block's CG starts from the previous block's
+ * last decoded frame (same solution, fewer iterations).  Errors: as
+ * mesh_codec_decode; MC_E_BITSTREAM_CORRUPT for a container whose sizes or
+ * flags do not match the handle. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_decode_blocks(mesh_codec_t* h, const uint8_t* in,
+                                                            size_t bytes, double* positions_out,
+                                                            void* stream);
 
 /* Same as encode / decode with HOST buffers: the call copies the input to
  * the device, runs the codec and copies the result back before returning.

@@ -43,7 +43,8 @@ class Params(ctypes.Structure):
         ("oi_tol", ctypes.c_double), ("cg_rtol", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("solve_mode", ctypes.c_int32),
         ("oi_refine_sweeps", ctypes.c_int32), ("autotune", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("block_delta", ctypes.c_int32), ("block_delta_bits", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -96,6 +97,10 @@ _SIGS = {
     "mesh_codec_decode_ex": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, _P, _P]),
     "mesh_codec_set_start_basis": (ctypes.c_int, [_P, _P, _P]),
     "mesh_codec_decode_stage": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, _P, _P]),
+    "mesh_codec_blocks_size": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "mesh_codec_encode_blocks": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_size_t,
+                                                ctypes.POINTER(ctypes.c_size_t), _P]),
+    "mesh_codec_decode_blocks": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, _P]),
     "mesh_codec_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_uint64, ctypes.POINTER(_P)]),
     "mesh_codec_mlp_param_count": (ctypes.c_size_t, [_P]),
@@ -271,6 +276,46 @@ class MeshCodec:
                                                ctypes.c_void_p(anc.data_ptr()), _stream_ptr(stream))
         _check(st, "mesh_codec_decode_stage")
         return delta, anc[:, :n_c]
+
+    # ------------------------------------------------------------ blocks variant
+    def blocks_size(self, n_blocks):
+        size = ctypes.c_size_t()
+        _check(self._lib.mesh_codec_blocks_size(self._h, int(n_blocks), ctypes.byref(size)),
+               "mesh_codec_blocks_size")
+        return size.value
+
+    def encode_blocks(self, positions, n_blocks, out=None, stream=None):
+        """positions: CUDA float64 [n_blocks * F, n, 3] -> CUDA uint8 container
+        (Section III-A: block 1 from the eigendecomposition of R[1], blocks
+        2..n_b from Algorithm 1's sweeps started at the previous basis)."""
+        torch = _torch()
+        assert positions.is_cuda and positions.dtype == torch.float64
+        assert tuple(positions.shape) == (n_blocks * self.F, self.n, 3)
+        assert positions.is_contiguous()
+        total = self.blocks_size(n_blocks)
+        if out is None:
+            out = torch.empty(total, dtype=torch.uint8, device=positions.device)
+        written = ctypes.c_size_t()
+        st = self._lib.mesh_codec_encode_blocks(self._h, ctypes.c_void_p(positions.data_ptr()),
+                                                int(n_blocks), ctypes.c_void_p(out.data_ptr()),
+                                                out.numel(), ctypes.byref(written),
+                                                _stream_ptr(stream))
+        _check(st, "mesh_codec_encode_blocks")
+        return out[: written.value]
+
+    def decode_blocks(self, container, n_blocks, out=None, stream=None, allow_not_converged=False):
+        """Container of encode_blocks -> CUDA float64 [n_blocks * F, n, 3]."""
+        torch = _torch()
+        assert container.is_cuda and container.dtype == torch.uint8
+        if out is None:
+            out = torch.empty((n_blocks * self.F, self.n, 3), dtype=torch.float64,
+                              device=container.device)
+        st = self._lib.mesh_codec_decode_blocks(self._h, ctypes.c_void_p(container.data_ptr()),
+                                                container.numel(), ctypes.c_void_p(out.data_ptr()),
+                                                _stream_ptr(stream))
+        if not (allow_not_converged and st == 6):
+            _check(st, "mesh_codec_decode_blocks")
+        return out
 
     def set_start_basis(self, q0=None, stream=None):
         """Orthogonal-iteration start basis: CUDA float64 [3, F, k] (made

@@ -23,6 +23,10 @@ using namespace mc;
 
 namespace {
 
+// the blocks variant's first block takes U[1] from the eigendecomposition of
+// R[1] = A A^T while its F x F matrix fits the Jacobi eigensolver
+constexpr int kDirectMaxFrames = MESH_CODEC_MAX_RANK;
+
 struct Carver {
   char* base;
   size_t off = 0;
@@ -80,6 +84,12 @@ size_t carve(mesh_codec* h, void* base) {
   h->Udeq = c.take<double>(3 * F * k);
   h->Cdeq = c.take<double>(3 * k * n);
   h->Ahat = c.take<double>(3 * nc * F);
+  h->Ublk = c.take<double>(3 * F * k);
+  h->Uhat = c.take<double>(3 * F * k);
+  const size_t Fd = F <= kDirectMaxFrames ? F : 1;
+  h->Rdir = c.take<double>(3 * Fd * Fd);
+  h->Vdir = c.take<double>(3 * Fd * Fd);
+  h->thetaF = c.take<double>(3 * Fd);
   h->cg.rz = c.take<double>(W);
   h->cg.rr = c.take<double>(W);
   h->cg.bb = c.take<double>(W);
@@ -152,7 +162,9 @@ bool valid_params(const mesh_codec_params_t* p) {
   if ((long long)p->n_frames * 3 > (1LL << 30)) return false;
   if ((long long)p->n_vertices * 3 * p->n_frames > (1LL << 40)) return false;
   if (p->autotune != 0 && p->autotune != 1) return false;
-  for (int i = 0; i < 5; ++i)
+  if (p->block_delta != 0 && p->block_delta != 1) return false;
+  if (p->block_delta_bits < 0 || p->block_delta_bits > MESH_CODEC_MAX_BITS) return false;
+  for (int i = 0; i < 3; ++i)
     if (p->reserved[i] != 0) return false;
   return true;
 }
@@ -230,7 +242,13 @@ static mesh_codec_status_t create_impl(mesh_codec* h, const int32_t* tris_in, in
     int sg = gemm_splits(F, ((k + 63) / 64) * ((k + 31) / 32));
     size_t a = (size_t)sz * 3 * F * k, b = (size_t)sh * 3 * k * k, c = (size_t)sg * 3 * k * k;
     h->partial_elems = std::max(a, std::max(b, c));
+    if (h->F <= kDirectMaxFrames) {   // R[1] = A A^T of the blocks variant
+      const int sd = gemm_splits(n, ((F + 63) / 64) * ((F + 31) / 32));
+      h->partial_elems = std::max(h->partial_elems, (size_t)sd * 3 * F * F);
+    }
   }
+  h->lay_delta = make_layout(n, h->F, h->k, h->n_c, h->p.coeff_bits, h->p.block_delta_bits,
+                             h->p.anchor_bits, h->kind);
   mixed_dims(h);
   h->ws_bytes = carve(h, nullptr);
   MC_TRY(cudaMalloc(&h->ws, h->ws_bytes));
@@ -353,9 +371,39 @@ mesh_codec_status_t mesh_codec_encoded_size(const mesh_codec_t* h, size_t* bytes
   return MC_OK;
 }
 
+// Options of one encode: the blocks variant supplies the start basis or the
+// direct eigendecomposition (Algorithm 1), a dictionary reference for the
+// difference coding of consecutive dictionaries, and that stream's layout.
+struct EncodeOpts {
+  const double* start = nullptr;       // start basis [3][F][k]; null: the handle's Q0
+  bool direct = false;                 // U = top-k eigenvectors of A A^T (F <= 64)
+  const double* dict_ref = nullptr;    // dictionary section codes U - dict_ref
+  const EncodeLayout* lay = nullptr;   // null: the handle's layout
+};
+
+__global__ void k_take_cols(const double* __restrict__ V, int rows, int ld, int cols,
+                            double* __restrict__ U) {
+  // U[c][r][j] = V[c][r][j] for j < cols (V: [3][rows][ld])
+  const long long total = 3LL * rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e / ((long long)rows * cols), rem = e % ((long long)rows * cols);
+    U[e] = V[(c * rows + rem / cols) * ld + rem % cols];
+  }
+}
+
+__global__ void k_axpy_sub(const double* __restrict__ a, const double* __restrict__ b,
+                           long long count, double sign, double* __restrict__ out) {
+  // out = a + sign * b (sign = -1: the coded difference; +1: the reconstruction)
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = sign > 0 ? __dadd_rn(a[e], b[e]) : __dsub_rn(a[e], b[e]);
+}
+
 static void enqueue_encode(mesh_codec* h, const double* positions, uint8_t* out, cudaStream_t s,
-                           Launches& L, bool host_check_tol) {
+                           Launches& L, bool host_check_tol, const EncodeOpts& o = EncodeOpts()) {
   const int n = h->n, F = h->F, k = h->k, W = h->W;
+  const EncodeLayout& lay = o.lay ? *o.lay : h->lay;
   cudaMemsetAsync(h->d_status, 0, sizeof(uint32_t), s);
   frames_to_vertex_major(positions, h->X, F, n, s, L);
   laplacian_rows(h->row_ptr, h->col_idx, h->deg, h->X, h->D, n, W, h->kind, s, L);
@@ -366,8 +414,21 @@ static void enqueue_encode(mesh_codec* h, const double* positions, uint8_t* out,
   const int sz = gemm_splits(n, ((F + 63) / 64) * ((k + 31) / 32));
   const int sh = gemm_splits(n, ((k + 63) / 64) * ((k + 31) / 32));
   const int sg = gemm_splits(F, ((k + 63) / 64) * ((k + 31) / 32));
-  cudaMemcpyAsync(h->Q, h->Q0, sizeof(double) * 3 * F * k, cudaMemcpyDeviceToDevice, s);
   for (int c = 0; c < 3; ++c) { h->oi_done[c] = 0; h->oi_last_change[c] = 0.0; }
+  if (o.direct) {
+    // Algorithm 1's first block: R = A_c A_c^T (F x F), its eigenvectors
+    // descending (Jacobi), the first k of them, signs
+    const int sd = gemm_splits(n, ((F + 63) / 64) * ((F + 31) / 32));
+    dgemm(F, F, n, 3, XcT, Xc, StridedOut{h->Rdir, F, 1, (long long)F * F}, sd, h->partials, s,
+          L);
+    jacobi_eig(h->Rdir, h->Vdir, h->thetaF, F, s, L);
+    k_take_cols<<<(3 * F * k + 255) / 256, 256, 0, s>>>(h->Vdir, F, F, k, h->U);
+    k_take_cols<<<1, 256, 0, s>>>(h->thetaF, 1, F, k, h->theta);
+    L.add(2);
+    sign_rule(h->U, F, k, s, L);
+  } else {
+  cudaMemcpyAsync(h->Q, o.start ? o.start : h->Q0, sizeof(double) * 3 * F * k,
+                  cudaMemcpyDeviceToDevice, s);
   // mixed precision: tensor-core sweeps first, then the FP64 refinement sweeps
   int fp64_sweeps = h->p.oi_sweeps;
   if (h->lp >= 0) {
@@ -404,6 +465,7 @@ static void enqueue_encode(mesh_codec* h, const double* positions, uint8_t* out,
   dgemm(F, k, k, 3, Strided{h->Q, k, 1, (long long)F * k}, Strided{h->V, k, 1, (long long)k * k},
         StridedOut{h->U, k, 1, (long long)F * k}, 1, nullptr, s, L);
   sign_rule(h->U, F, k, s, L);
+  }
   // projection C_c = U_c^T delta_c^T (k x n)
   if (h->lp >= 0) {
     mixed_project(h, s, L);
@@ -411,15 +473,25 @@ static void enqueue_encode(mesh_codec* h, const double* positions, uint8_t* out,
     dgemm(k, n, F, 3, Strided{h->U, 1, k, (long long)F * k}, Strided{h->D, 1, W, F},
           StridedOut{h->Cf, n, 1, (long long)k * n}, 1, nullptr, s, L);
   }
+  // the coded dictionary: U, or its difference from the reference (into Zb,
+  // free after the sweeps)
+  const double* Ucode = h->U;
+  if (o.dict_ref) {
+    const long long cnt = 3LL * F * k;
+    k_axpy_sub<<<(int)std::min<long long>((cnt + 255) / 256, 1024), 256, 0, s>>>(
+        h->U, o.dict_ref, cnt, -1.0, h->Zb);
+    L.add(1);
+    Ucode = h->Zb;
+  }
   // quantizer ranges: dictionary columns, coefficient rows, anchors
   const long long P = 4LL * k + 2;
-  minmax_rows_out(h->U, k, F, 1, k, 3, (long long)F * k, h->qparams, h->qparams + k, P, s, L);
+  minmax_rows_out(Ucode, k, F, 1, k, 3, (long long)F * k, h->qparams, h->qparams + k, P, s, L);
   minmax_rows_out(h->Cf, k, n, n, 1, 3, (long long)k * n, h->qparams + 2 * k, h->qparams + 3 * k,
                   P, s, L);
   anchor_minmax_out(h->X, h->anchors, h->n_c, F, h->qparams + 4 * k, h->qparams + 4 * k + 1, P,
                     s, L);
-  write_header(out, h->lay, h->anchors, h->qparams, s, L);
-  quant_pack_sections(out, h->lay, h->U, h->Cf, h->X, h->anchors, h->qparams, s, L);
+  write_header(out, lay, h->anchors, h->qparams, s, L);
+  quant_pack_sections(out, lay, Ucode, h->Cf, h->X, h->anchors, h->qparams, s, L);
 }
 
 mesh_codec_status_t mesh_codec_encode(mesh_codec_t* h, const double* positions, uint8_t* bitstream,
@@ -437,12 +509,13 @@ mesh_codec_status_t mesh_codec_encode(mesh_codec_t* h, const double* positions, 
   return read_status(h, s);
 }
 
-static mesh_codec_status_t check_header(mesh_codec* h, const uint8_t* hdr, size_t bytes) {
+static mesh_codec_status_t check_header(mesh_codec* h, const uint8_t* hdr, size_t bytes,
+                                        const EncodeLayout* lay = nullptr) {
   uint32_t w[8];
   std::memcpy(w, hdr, 32);
   unsigned long long total;
   std::memcpy(&total, hdr + 32, 8);
-  const EncodeLayout& L = h->lay;
+  const EncodeLayout& L = lay ? *lay : h->lay;
   if (w[0] != 0x31434D44u || w[1] != 1u || w[7] != 64u) return MC_E_BITSTREAM_CORRUPT;
   if ((int)w[2] != L.n || (int)w[3] != L.F || (int)w[4] != L.k || (int)w[5] != L.n_c)
     return MC_E_BITSTREAM_CORRUPT;
@@ -496,12 +569,19 @@ __global__ void k_flag_not_converged(const int32_t* done, int W, uint32_t* statu
 // solves in lockstep on their own streams (mesh_codec_decode_batch).
 // Phase 1: unpack, back-projection, right-hand sides, CG start.
 static void decode_prepare(mesh_codec* h, const uint8_t* in, cudaStream_t s, Launches& L,
-                           const double* x0 = nullptr) {
+                           const double* x0 = nullptr, const double* dict_ref = nullptr,
+                           const EncodeLayout* lay = nullptr) {
   const int n = h->n, F = h->F, k = h->k, W = h->W;
   DecodeState& d = h->dec;
   cudaMemsetAsync(h->d_status, 0, sizeof(uint32_t), s);
-  unpack_sections(in, h->lay, h->Udeq, h->Cdeq, h->Ahat, h->dec_anchors, nullptr, h->d_status, s,
-                  L);
+  unpack_sections(in, lay ? *lay : h->lay, h->Udeq, h->Cdeq, h->Ahat, h->dec_anchors, nullptr,
+                  h->d_status, s, L);
+  if (dict_ref) {   // the dictionary section holds differences from dict_ref
+    const long long cnt = 3LL * F * k;
+    k_axpy_sub<<<(int)std::min<long long>((cnt + 255) / 256, 1024), 256, 0, s>>>(
+        h->Udeq, dict_ref, cnt, 1.0, h->Udeq);
+    L.add(1);
+  }
   // the decoder's anchor set comes from the stream
   cudaMemsetAsync(h->is_anchor, 0, n, s);
   mark_anchors(h->dec_anchors, h->n_c, h->is_anchor, s, L);
@@ -658,8 +738,10 @@ static void decode_finish(mesh_codec* h, double* out, cudaStream_t s, Launches& 
 
 static mesh_codec_status_t enqueue_decode(mesh_codec* h, const uint8_t* in, double* out,
                                           cudaStream_t s, Launches& L,
-                                          const double* x0 = nullptr) {
-  decode_prepare(h, in, s, L, x0);
+                                          const double* x0 = nullptr,
+                                          const double* dict_ref = nullptr,
+                                          const EncodeLayout* lay = nullptr) {
+  decode_prepare(h, in, s, L, x0, dict_ref, lay);
   while (decode_cg_chunk(h, 32, s, L)) {
     MC_TRY(cudaStreamSynchronize(s));
     if (*h->h_active == 0) break;
@@ -753,6 +835,150 @@ mesh_codec_status_t mesh_codec_set_start_basis(mesh_codec_t* h, const double* q0
   cholqr3(h->Q0, h->F, h->k, qr_work(h, sg), nullptr, h->d_status, s, L);
   MC_TRY(cudaGetLastError());
   return read_status(h, s);
+}
+
+// ------------------------------------------------------------ blocks variant
+static constexpr uint32_t kBlocksMagic = 0x42434D44u;   // "DMCB"
+
+struct BlocksSizes {
+  unsigned long long first, other, total;
+};
+
+static BlocksSizes blocks_sizes(const mesh_codec* h, int n_blocks) {
+  BlocksSizes z;
+  z.first = (unsigned long long)h->lay.total;
+  z.other = (unsigned long long)(h->p.block_delta ? h->lay_delta.total : h->lay.total);
+  z.total = 64ull + z.first + (unsigned long long)(n_blocks - 1) * z.other;
+  return z;
+}
+
+mesh_codec_status_t mesh_codec_blocks_size(const mesh_codec_t* h, int n_blocks, size_t* bytes) {
+  if (!h || !bytes || n_blocks < 1) return MC_E_INVALID_ARG;
+  *bytes = (size_t)blocks_sizes(h, n_blocks).total;
+  return MC_OK;
+}
+
+mesh_codec_status_t mesh_codec_encode_blocks(mesh_codec_t* h, const double* positions,
+                                             int n_blocks, uint8_t* out, size_t capacity,
+                                             size_t* written, void* stream) {
+  if (!h || !positions || !out || !written || n_blocks < 1) return MC_E_INVALID_ARG;
+  if (((uintptr_t)out & 7) || ((uintptr_t)positions & 7)) return MC_E_INVALID_ARG;
+  const BlocksSizes z = blocks_sizes(h, n_blocks);
+  *written = (size_t)z.total;
+  if (capacity < z.total) return MC_E_BUFFER_TOO_SMALL;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  h->launches_encode = 0;
+  Launches L{&h->launches_encode};
+  const int n = h->n, F = h->F, k = h->k;
+  const bool delta = h->p.block_delta != 0;
+  const size_t basis_bytes = sizeof(double) * 3 * F * k;
+  // container header, staged in pinned memory (read_status below waits for the copy)
+  std::memset(h->h_header, 0, 64);
+  const uint32_t w[5] = {kBlocksMagic, 1u, (uint32_t)n_blocks, delta ? 1u : 0u,
+                         delta ? (uint32_t)h->p.block_delta_bits : 0u};
+  const unsigned long long q[3] = {z.first, z.other, z.total};
+  std::memcpy(h->h_header, w, sizeof(w));
+  std::memcpy(h->h_header + sizeof(w), q, sizeof(q));
+  MC_TRY(cudaMemcpyAsync(out, h->h_header, 64, cudaMemcpyHostToDevice, s));
+  size_t off = 64;
+  for (int b = 0; b < n_blocks; ++b) {
+    const double* pos_b = positions + (size_t)b * F * n * 3;
+    uint8_t* out_b = out + off;
+    const bool dref = delta && b > 0;
+    EncodeOpts o;
+    if (b == 0) o.direct = F <= kDirectMaxFrames;   // Algorithm 1's SVD of R[1]
+    else o.start = h->Ublk;                          // U[i]^(1) = U[i-1]
+    if (dref) {
+      o.dict_ref = h->Uhat;
+      o.lay = &h->lay_delta;
+    }
+    enqueue_encode(h, pos_b, out_b, s, L, false, o);
+    MC_TRY(cudaGetLastError());
+    mesh_codec_status_t st = read_status(h, s);
+    if (st != MC_OK) return st;
+    MC_TRY(cudaMemcpyAsync(h->Ublk, h->U, basis_bytes, cudaMemcpyDeviceToDevice, s));
+    if (delta) {
+      // the dictionary the decoder will hold after this block (closed loop)
+      unpack_sections(out_b, dref ? h->lay_delta : h->lay, h->Udeq, h->Cdeq, h->Ahat,
+                      h->dec_anchors, nullptr, h->d_status, s, L);
+      if (dref) {
+        const long long cnt = 3LL * F * k;
+        k_axpy_sub<<<(int)std::min<long long>((cnt + 255) / 256, 1024), 256, 0, s>>>(
+            h->Udeq, h->Uhat, cnt, 1.0, h->Uhat);
+        L.add(1);
+      } else {
+        MC_TRY(cudaMemcpyAsync(h->Uhat, h->Udeq, basis_bytes, cudaMemcpyDeviceToDevice, s));
+      }
+    }
+    off += (size_t)(b == 0 ? z.first : z.other);
+  }
+  MC_TRY(cudaGetLastError());
+  return read_status(h, s);
+}
+
+mesh_codec_status_t mesh_codec_decode_blocks(mesh_codec_t* h, const uint8_t* in, size_t bytes,
+                                             double* positions_out, void* stream) {
+  if (!h || !in || !positions_out) return MC_E_INVALID_ARG;
+  if (((uintptr_t)in & 7) || ((uintptr_t)positions_out & 7)) return MC_E_INVALID_ARG;
+  if (bytes < 64) return MC_E_BITSTREAM_CORRUPT;
+  if (h->n_c == 0) return MC_E_INVALID_ARG;   // Eq. 12 needs anchors
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  MC_TRY(cudaMemcpyAsync(h->h_header, in, 64, cudaMemcpyDeviceToHost, s));
+  MC_TRY(cudaStreamSynchronize(s));
+  uint32_t w[5];
+  unsigned long long q[3];
+  std::memcpy(w, h->h_header, sizeof(w));
+  std::memcpy(q, h->h_header + sizeof(w), sizeof(q));
+  if (w[0] != kBlocksMagic || w[1] != 1u || w[2] < 1u || w[2] > (1u << 24) || (w[3] & ~1u))
+    return MC_E_BITSTREAM_CORRUPT;
+  const int n_blocks = (int)w[2];
+  const bool delta = (w[3] & 1u) != 0;
+  if (delta != (h->p.block_delta != 0) || (delta && (int)w[4] != h->p.block_delta_bits))
+    return MC_E_BITSTREAM_CORRUPT;
+  const BlocksSizes z = blocks_sizes(h, n_blocks);
+  if (q[0] != z.first || q[1] != z.other || q[2] != z.total || bytes != (size_t)z.total)
+    return MC_E_BITSTREAM_CORRUPT;
+  const int n = h->n, F = h->F, k = h->k;
+  const bool frames = !use_factored(h);
+  h->launches_decode = 0;
+  Launches L{&h->launches_decode};
+  mesh_codec_status_t worst = MC_OK;
+  size_t off = 64;
+  for (int b = 0; b < n_blocks; ++b) {
+    const uint8_t* in_b = in + off;
+    const size_t nbytes = (size_t)(b == 0 ? z.first : z.other);
+    const bool dref = delta && b > 0;
+    const EncodeLayout* lay = dref ? &h->lay_delta : &h->lay;
+    MC_TRY(cudaMemcpyAsync(h->h_header, in_b, 64, cudaMemcpyDeviceToHost, s));
+    MC_TRY(cudaStreamSynchronize(s));
+    mesh_codec_status_t st = check_header(h, h->h_header, nbytes, lay);
+    if (st != MC_OK) return st;
+    double* out_b = positions_out + (size_t)b * F * n * 3;
+    const double* x0 = nullptr;
+    if (frames && b > 0) {
+      // the previous block's last decoded frame, repeated, as the first iterate
+      // (R is free until the CG starts)
+      st = mesh_codec_warm_compose(n, F, out_b - (size_t)n * 3, nullptr, h->R, s);
+      if (st != MC_OK) return st;
+      L.add(1);
+      x0 = h->R;
+    }
+    st = enqueue_decode(h, in_b, out_b, s, L, x0, dref ? h->Uhat : nullptr, lay);
+    if (st != MC_OK) return st;
+    MC_TRY(cudaGetLastError());
+    st = read_status(h, s);
+    if (st == MC_E_NOT_CONVERGED) worst = st;
+    else if (st != MC_OK) return st;
+    if (delta)
+      MC_TRY(cudaMemcpyAsync(h->Uhat, h->Udeq, sizeof(double) * 3 * F * k,
+                             cudaMemcpyDeviceToDevice, s));
+    off += nbytes;
+  }
+  MC_TRY(cudaStreamSynchronize(s));
+  prof_collect(h);
+  return worst;
 }
 
 static mesh_codec_status_t ensure_staging(mesh_codec* h) {

@@ -19,6 +19,7 @@ struct mesh_codec {
   mesh_codec_params_t p;
   int n, T, F, k, W, n_c, kind;
   mc::EncodeLayout lay;
+  mc::EncodeLayout lay_delta;      // blocks 2..n_b with dictionary differences
   mc::CgGeom geom;
   // device workspace (one allocation)
   void* ws = nullptr;
@@ -34,6 +35,10 @@ struct mesh_codec {
   double *Cf, *qparams;
   double *X, *D, *B, *R, *P, *Tv, *Qv;
   double *Udeq, *Cdeq, *Ahat;
+  // blocks variant: the previous block's exact basis (Algorithm 1's start)
+  // and the decoder's dequantized previous dictionary [3][F][k]; the direct
+  // eigendecomposition of R[1] = A A^T: R and V [3][F][F], eigenvalues [3][F]
+  double *Ublk, *Uhat, *Rdir, *Vdir, *thetaF;
   mc::CgState cg;
   uint32_t* d_status;
   int nnz;

@@ -86,6 +86,11 @@ def test_invalid_params_rejected_before_any_device_work(lib):
     assert lib.mesh_codec_create(ctypes.byref(p), ctypes.cast(tris, ctypes.c_void_p), 0, None, 0,
                                  None, ctypes.byref(h)) == 1
     p.coeff_bits = 12
+    for field, bad in (("block_delta", 2), ("block_delta_bits", 32), ("block_delta_bits", -1)):
+        setattr(p, field, bad)
+        assert lib.mesh_codec_create(ctypes.byref(p), ctypes.cast(tris, ctypes.c_void_p), 0, None,
+                                     0, None, ctypes.byref(h)) == 1
+        setattr(p, field, 0)
     p.reserved[0] = 1
     assert lib.mesh_codec_create(ctypes.byref(p), ctypes.cast(tris, ctypes.c_void_p), 0, None, 0,
                                  None, ctypes.byref(h)) == 1
