@@ -235,6 +235,22 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_set_start_basis(mesh_codec_t* h, c
 MESH_CODEC_API mesh_codec_status_t mesh_codec_blocks_size(const mesh_codec_t* h, int n_blocks,
                                                           size_t* bytes);
 
+/* Bits per vertex and frame of the streams a handle with parameters *p
+ * writes, for n_blocks blocks of p->n_frames frames (1: a plain stream), as
+ * the terms of Eq. 13 for what the stream holds (k of the F dictionary
+ * columns per block):
+ *   out[0] q   = coeff_bits * k / F
+ *   out[1] q_a = anchor_bits * n_c / n
+ *   out[2] q_d = dictionary bits * k / n, averaged over the blocks (block 1
+ *                dict_bits; blocks 2..n_b block_delta_bits when block_delta)
+ *   out[3] q_s = q + q_a + q_d
+ *   out[4] the stream's own rate: its bytes * 8 / (n * F * n_blocks), with
+ *          headers, anchor indices, quantizer ranges and padding
+ * (a bit count of 0 means raw binary64: 64 bits).  Host arithmetic only: no
+ * device is used.  Errors: MC_E_INVALID_ARG. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_rates(const mesh_codec_params_t* p, int n_blocks,
+                                                    double* out);
+
 /* positions: device float64 [n_blocks * F][n][3]; out: device, 8-byte
  * aligned, `capacity` bytes; *written = the container size (also on
  * MC_E_BUFFER_TOO_SMALL).  Leaves the handle's start basis unchanged.

@@ -101,6 +101,7 @@ _SIGS = {
     "mesh_codec_encode_blocks": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_size_t,
                                                 ctypes.POINTER(ctypes.c_size_t), _P]),
     "mesh_codec_decode_blocks": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, _P]),
+    "mesh_codec_rates": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int, _P]),
     "mesh_codec_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_uint64, ctypes.POINTER(_P)]),
     "mesh_codec_mlp_param_count": (ctypes.c_size_t, [_P]),
@@ -676,3 +677,17 @@ def basis_compose(U_prev, pred=None, stream=None):
         None if pred is None else _dptr(pred, torch.float32, (3 * F, k)), _dptr(q0),
         _stream_ptr(stream)), "mesh_codec_basis_compose")
     return q0
+
+
+def rates(n_blocks=1, **kw):
+    """Eq. 13's bits per vertex and frame for a stream of the given
+    parameters (see mesh_codec_rates): {q, q_a, q_d, q_s, stream}."""
+    p = default_params()
+    for key, val in kw.items():
+        if not hasattr(p, key):
+            raise TypeError(f"unknown parameter {key}")
+        setattr(p, key, val)
+    out = (ctypes.c_double * 5)()
+    _check(load_library().mesh_codec_rates(ctypes.byref(p), int(n_blocks),
+                                           ctypes.cast(out, ctypes.c_void_p)), "mesh_codec_rates")
+    return dict(zip(("q", "q_a", "q_d", "q_s", "stream"), list(out)))

@@ -858,6 +858,31 @@ mesh_codec_status_t mesh_codec_blocks_size(const mesh_codec_t* h, int n_blocks, 
   return MC_OK;
 }
 
+mesh_codec_status_t mesh_codec_rates(const mesh_codec_params_t* p, int n_blocks, double* out) {
+  if (!out || n_blocks < 1 || !valid_params(p)) return MC_E_INVALID_ARG;
+  const double n = p->n_vertices, F = p->n_frames, k = p->rank, nc = p->n_anchors;
+  auto bits = [](int b) { return b == 0 ? 64.0 : (double)b; };
+  const bool delta = p->block_delta != 0;
+  const double db_first = bits(p->dict_bits);
+  const double db_other = delta ? bits(p->block_delta_bits) : db_first;
+  out[0] = bits(p->coeff_bits) * k / F;
+  out[1] = bits(p->anchor_bits) * nc / n;
+  out[2] = (db_first + (n_blocks - 1) * db_other) * k / (n * n_blocks);
+  out[3] = out[0] + out[1] + out[2];
+  const EncodeLayout first = make_layout(p->n_vertices, p->n_frames, p->rank, p->n_anchors,
+                                         p->coeff_bits, p->dict_bits, p->anchor_bits,
+                                         p->laplacian_kind);
+  const EncodeLayout other = make_layout(p->n_vertices, p->n_frames, p->rank, p->n_anchors,
+                                         p->coeff_bits,
+                                         delta ? p->block_delta_bits : p->dict_bits,
+                                         p->anchor_bits, p->laplacian_kind);
+  const double bytes = n_blocks == 1
+                           ? (double)first.total
+                           : 64.0 + (double)first.total + (n_blocks - 1.0) * (double)other.total;
+  out[4] = bytes * 8.0 / (n * F * n_blocks);
+  return MC_OK;
+}
+
 mesh_codec_status_t mesh_codec_encode_blocks(mesh_codec_t* h, const double* positions,
                                              int n_blocks, uint8_t* out, size_t capacity,
                                              size_t* written, void* stream) {

@@ -106,3 +106,34 @@ def test_stream_size_formula_matches_oracle(lib):
     assert oc.stream_size(2562, 64, 16, 20, 12, 16, 16) == 64 + 80 + 3 * (
         8 * 66 + ((64 * 16 + 31) // 32) * 16 * 4 + ((16 * 2562 + 31) // 32) * 12 * 4 +
         ((20 * 64 + 31) // 32) * 16 * 4)
+
+
+@pytest.mark.parametrize("n_blocks,delta", [(1, 0), (4, 0), (4, 1)])
+def test_rates_match_the_oracle(lib, n_blocks, delta):
+    # host-only entry point: Eq. 13's terms for what the stream holds, and the
+    # stream's own rate from its size, against the oracle's formulas
+    from oracle import blocks as ob, codec as oc, metrics
+    from paper_2111_10105_gb300.codec import Params, default_params
+    lib.mesh_codec_rates.restype = ctypes.c_int
+    lib.mesh_codec_rates.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_void_p]
+    p = default_params()
+    p.n_vertices, p.n_triangles, p.n_frames, p.rank, p.n_anchors = 10002, 20000, 175, 20, 100
+    p.block_delta, p.block_delta_bits = delta, 10 if delta else 0
+    out = (ctypes.c_double * 5)()
+    assert lib.mesh_codec_rates(ctypes.byref(p), n_blocks, out) == 0
+    r = metrics.rates(10002, 175, 20, 100, 12, 16, 16, n_b=1, dict_cols=20)
+    assert out[0] == pytest.approx(r["q"], rel=1e-15)
+    assert out[1] == pytest.approx(r["q_a"], rel=1e-15)
+    # Table I's anchor rate: 16 bits, 1% anchors, n = 10002 (Handstand)
+    assert round(out[1], 4) == 0.1600
+    dict_bits = [16] + [10 if delta else 16] * (n_blocks - 1)
+    assert out[2] == pytest.approx(sum(dict_bits) * 20 / (10002 * n_blocks), rel=1e-15)
+    assert out[3] == pytest.approx(out[0] + out[1] + out[2], rel=1e-15)
+    op = oc.Params(n_frames=175, rank=20, n_anchors=100)
+    if n_blocks == 1:
+        nbytes = oc.stream_size(10002, 175, 20, 100, 12, 16, 16)
+    else:
+        nbytes = ob.container_size(10002, op, n_blocks, bool(delta), 10)[0]
+    assert out[4] == pytest.approx(nbytes * 8 / (10002 * 175 * n_blocks), rel=1e-15)
+    p.rank = 0
+    assert lib.mesh_codec_rates(ctypes.byref(p), 1, out) == 1
