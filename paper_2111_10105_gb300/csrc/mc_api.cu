@@ -103,6 +103,7 @@ size_t carve(mesh_codec* h, void* base) {
   h->cg.active = c.take<int32_t>(1);
   h->cg.all_done = c.take<int32_t>(1);
   h->d_status = c.take<uint32_t>(4);
+  h->d_match = c.take<int32_t>(1);
   size_t off = mixed_carve(h, (char*)base, c.off);
   return off + 1024;
 }
@@ -210,6 +211,8 @@ void mesh_codec_destroy(mesh_codec_t* h) {
   if (!h) return;
   cudaDeviceSynchronize();
   if (h->ws) cudaFree(h->ws);
+  if (h->Gcache) cudaFree(h->Gcache);
+  if (h->Gcache_anchors) cudaFree(h->Gcache_anchors);
   if (h->stage_pos) cudaFree(h->stage_pos);
   if (h->stage_bits) cudaFree(h->stage_bits);
   if (h->h_status) cudaFreeHost(h->h_status);
@@ -565,6 +568,30 @@ static bool use_factored(const mesh_codec* h) {
 
 __global__ void k_flag_not_converged(const int32_t* done, int W, uint32_t* status);
 
+// *count += number of positions where a and b differ
+__global__ void k_count_mismatch(const int32_t* __restrict__ a, const int32_t* __restrict__ b,
+                                 int count, int32_t* out) {
+  int diff = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+    diff += a[i] != b[i];
+  if (diff) atomicAdd(out, diff);
+}
+
+// G[i][a] = X[i][col0 + a] for a < cols (X: [n][ld])
+__global__ void k_copy_cols(const double* __restrict__ X, int ld, int col0, int n, int cols,
+                            double* __restrict__ G) {
+  const long long total = (long long)n * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    G[e] = X[(e / cols) * ld + col0 + e % cols];
+}
+
+// the kept anchor response becomes usable once its decode converged
+static void settle_anchor_cache(mesh_codec* h, mesh_codec_status_t st) {
+  if (h->Gcache_pending) h->Gcache_valid = st == MC_OK;
+  h->Gcache_pending = false;
+}
+
 // Decoder, in three phases so that several handles can advance their CG
 // solves in lockstep on their own streams (mesh_codec_decode_batch).
 // Phase 1: unpack, back-projection, right-hand sides, CG start.
@@ -588,10 +615,23 @@ static void decode_prepare(mesh_codec* h, const uint8_t* in, cudaStream_t s, Lau
   vertex_scalars_marked(h->row_ptr, h->col_idx, h->deg, h->is_anchor, n, h->kind, h->inv_d,
                         h->inv_diag, s, L);
   d.factored = use_factored(h);
-  // CG columns: 3F frames (Eq. 11-12 as written), or 3k + n_c factored columns
-  // (the FP32 factored solve pads its column count to a multiple of 4 with
-  // zero right-hand sides, which converge at once, for the float4 kernels)
-  d.Wc = d.factored ? 3 * k + h->n_c : W;
+  // the kept anchor response applies when this stream's anchors are its anchors
+  d.cached = false;
+  if (d.factored && h->Gcache_valid) {
+    cudaMemsetAsync(h->d_match, 0, sizeof(int32_t), s);
+    k_count_mismatch<<<(h->n_c + 255) / 256, 256, 0, s>>>(h->dec_anchors, h->Gcache_anchors,
+                                                          h->n_c, h->d_match);
+    L.add(1);
+    cudaMemcpyAsync(h->h_active + 1, h->d_match, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    d.cached = h->h_active[1] == 0;
+  }
+  d.store = d.factored && !d.cached;
+  // CG columns: 3F frames (Eq. 11-12 as written), or 3k + n_c factored columns,
+  // or the 3k data columns with the kept anchor response (the FP32 factored
+  // solve pads its column count to a multiple of 4 with zero right-hand
+  // sides, which converge at once, for the float4 kernels)
+  d.Wc = d.factored ? (d.cached ? 3 * k : 3 * k + h->n_c) : W;
   if (d.factored && h->lp >= 0) d.Wc = (d.Wc + 3) / 4 * 4;
   if (!d.factored) {
     // delta~_c = (U_c' C_c')^T : (n x k)(k x F) into D[:, cF : cF + F]
@@ -613,7 +653,7 @@ static void decode_prepare(mesh_codec* h, const uint8_t* in, cudaStream_t s, Lau
     factored_rhs(h->Cdeq, k, n, d.Wc, h->D, s, L);
     laplacian_t_rows(h->row_ptr, h->col_idx, h->deg, h->inv_d, h->D, h->B, n, d.Wc, h->kind, s,
                      L);
-    unit_anchor_columns(h->B, h->dec_anchors, h->n_c, d.Wc, 3 * k, s, L);
+    if (!d.cached) unit_anchor_columns(h->B, h->dec_anchors, h->n_c, d.Wc, 3 * k, s, L);
   }
   // CG: FP64 vectors, or FP32 vectors with FP64-accurate dot products in the mixed modes
   d.single = h->lp >= 0 ? 1 : 0;
@@ -727,9 +767,33 @@ static void decode_finish(mesh_codec* h, double* out, cudaStream_t s, Launches& 
           StridedOut{h->D, W, 1, F}, 1, nullptr, s, L);
     StridedOut acc{h->D, W, 1, F};
     acc.accumulate = 1;
-    dgemm(n, F, h->n_c, 3, Strided{Xs + 3 * k, d.Wc, 1, 0},
-          Strided{h->Ahat, F, 1, (long long)std::max(h->n_c, 1) * F}, acc, 1, nullptr, s, L);
+    const Strided G = d.cached ? Strided{h->Gcache, h->n_c, 1, 0}
+                               : Strided{Xs + 3 * k, d.Wc, 1, 0};
+    dgemm(n, F, h->n_c, 3, G, Strided{h->Ahat, F, 1, (long long)std::max(h->n_c, 1) * F}, acc, 1,
+          nullptr, s, L);
     vertex_major_to_frames(h->D, out, F, n, s, L);
+    if (d.store) {
+      // keep G and its anchors; valid once the decode reports every column converged
+      if (!h->Gcache) {
+        if (cudaMalloc(&h->Gcache, sizeof(double) * (size_t)n * h->n_c) != cudaSuccess ||
+            cudaMalloc(&h->Gcache_anchors, sizeof(int32_t) * h->n_c) != cudaSuccess) {
+          cudaGetLastError();
+          if (h->Gcache) cudaFree(h->Gcache);
+          h->Gcache = nullptr;
+          h->Gcache_anchors = nullptr;
+        }
+      }
+      if (h->Gcache) {
+        h->Gcache_valid = false;
+        const long long cnt = (long long)n * h->n_c;
+        k_copy_cols<<<(int)std::min<long long>((cnt + 255) / 256, 4096), 256, 0, s>>>(
+            Xs, d.Wc, 3 * k, n, h->n_c, h->Gcache);
+        cudaMemcpyAsync(h->Gcache_anchors, h->dec_anchors, sizeof(int32_t) * h->n_c,
+                        cudaMemcpyDeviceToDevice, s);
+        L.add(1);
+        h->Gcache_pending = true;
+      }
+    }
   }
   k_flag_not_converged<<<(h->cg_columns + 255) / 256, 256, 0, s>>>(h->cg.done, h->cg_columns,
                                                                      h->d_status);
@@ -779,6 +843,7 @@ mesh_codec_status_t mesh_codec_decode_ex(mesh_codec_t* h, const uint8_t* bitstre
   if (st != MC_OK) return st;
   MC_TRY(cudaGetLastError());
   st = read_status(h, s);
+  settle_anchor_cache(h, st);
   prof_collect(h);
   return st;
 }
@@ -994,6 +1059,7 @@ mesh_codec_status_t mesh_codec_decode_blocks(mesh_codec_t* h, const uint8_t* in,
     if (st != MC_OK) return st;
     MC_TRY(cudaGetLastError());
     st = read_status(h, s);
+    settle_anchor_cache(h, st);
     if (st == MC_E_NOT_CONVERGED) worst = st;
     else if (st != MC_OK) return st;
     if (delta)
@@ -1053,6 +1119,7 @@ mesh_codec_status_t mesh_codec_decode_host(mesh_codec_t* h, const uint8_t* bitst
                          cudaMemcpyDeviceToHost, s));
   MC_TRY(cudaGetLastError());
   st = read_status(h, s);
+  settle_anchor_cache(h, st);
   prof_collect(h);
   return st;
 }
@@ -1180,6 +1247,7 @@ mesh_codec_status_t mesh_codec_decode_batch(mesh_codec_t* const* handles, int co
       st[i] = read_status(handles[i], handles[i]->own);
       prof_collect(handles[i]);
     }
+    settle_anchor_cache(handles[i], st[i]);
     if (statuses) statuses[i] = st[i];
     if (first == MC_OK) first = st[i];
   }

@@ -9,6 +9,8 @@
 // per-decode state carried between the decoder's phases
 struct DecodeState {
   bool factored = false;
+  bool cached = false;           // factored solve with the kept anchor response G
+  bool store = false;            // this decode computes G and may keep it
   int Wc = 0, single = 0, it = 0;
   mc::CgGeom geom{};
   const void* inv_d = nullptr;
@@ -39,6 +41,15 @@ struct mesh_codec {
   // and the decoder's dequantized previous dictionary [3][F][k]; the direct
   // eigendecomposition of R[1] = A A^T: R and V [3][F][F], eigenvalues [3][F]
   double *Ublk, *Uhat, *Rdir, *Vdir, *thetaF;
+  // Anchor response of the factored solve, G = M^-1 P^T ([n][n_c] FP64): it
+  // depends only on the connectivity and the anchor set, so the handle keeps
+  // the G of its last complete factored decode (own allocation, made on first
+  // use) together with that decode's anchors, and later decodes with the
+  // same anchors solve only the 3k data columns.
+  double* Gcache = nullptr;
+  int32_t* Gcache_anchors = nullptr;
+  bool Gcache_valid = false, Gcache_pending = false;
+  int32_t* d_match = nullptr;      // device: anchors differing from the kept set
   mc::CgState cg;
   uint32_t* d_status;
   int nnz;
