@@ -299,11 +299,13 @@ def run_ours(args):
     F, n = pos.shape[0], pos.shape[1]
     prec = PRECISION_CODE[args.precision]
     single = prec != 0
-    cg_rtol = 1e-6 if single else 1e-14
+    # the FP32 solve stops at 1e-6; FP64 and the refined solve (FP64 residuals) at 1e-14
+    cg_rtol = 1e-6 if (single and not args.refine) else 1e-14
+    single = single or args.refine > 0      # the CG sweeps run on FP32 vectors
     kw = dict(n_frames=F, rank=spec.rank, n_anchors=spec.n_anchors, seed=spec.seed,
               coeff_bits=spec.coeff_bits, dict_bits=spec.dict_bits,
               anchor_bits=spec.anchor_bits, oi_sweeps=SWEEPS, precision=prec,
-              oi_refine_sweeps=1 if single else 0, cg_rtol=cg_rtol,
+              oi_refine_sweeps=1 if prec else 0, cg_rtol=cg_rtol, refine=args.refine,
               solve_mode={"frames": 0, "factored": 1}[args.solve_mode])
     mc = MeshCodec(tris, n, **kw)
     pos_dev = torch.from_numpy(pos).to(dev)
@@ -386,13 +388,15 @@ def run_ours(args):
             "ms_per_step": seconds * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "tf32": "tf32+f32 (FP64 QR, refinement, quantizer)",
-                      "bf16": "bf16+f32 (FP64 QR, refinement, quantizer)"}[args.precision],
+                      "bf16": "bf16+f32 (FP64 QR, refinement, quantizer)"}[args.precision]
+                     + (f"; solve: FP64 residuals, FP32 CG corrections to 1e-{args.refine}"
+                        if args.refine else ""),
             "data": "synthetic",
             "config": {"workload": args.workload, "mesh": spec.mesh, "n": n, "F": F,
                        "k": spec.rank, "anchors": spec.n_anchors,
                        "bits": [spec.coeff_bits, spec.dict_bits, spec.anchor_bits],
                        "oi_sweeps": SWEEPS, "oi_refine_sweeps": 1 if single else 0,
-                       "cg_rtol": cg_rtol, "precision": args.precision,
+                       "cg_rtol": cg_rtol, "precision": args.precision, "refine": args.refine,
                        "decode_columns": cols, "solve_mode": args.solve_mode,
                        "l2": "flushed (256 MiB write) before every step",
                        "parallelism": f"replicas x{world}"},
@@ -504,6 +508,106 @@ def run_batched(args):
         print(json.dumps(out), flush=True)
     for c in codecs:
         c.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_blocks(args):
+    """The torus sequence (20,000 vertices, 256 frames) coded as n_b = 8 blocks
+    of 32 frames (Section III-A, Algorithm 1: block 1 from the eigenvectors of
+    R[1], blocks 2..8 from 8 sweeps started at the previous basis, k = 16 per
+    block), against one block (k = 32, the default workload's settings) on
+    the same frames: the comparison of Table II's "blocks" column, with the
+    rates of Eq. 13 and the NMSE of both."""
+    import torch
+
+    from oracle import metrics
+    from paper_2111_10105_gb300 import MeshCodec, codec as cb
+    from synth import make_sequence, config_spec
+
+    world, rank, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = config_spec(DEFAULT_WORKLOAD)
+    tris, pos = make_sequence(spec)
+    F, n = pos.shape[0], pos.shape[1]
+    nb, kf, kb = 8, F // 8, spec.rank // 2
+    common = dict(n_anchors=spec.n_anchors, seed=spec.seed, coeff_bits=spec.coeff_bits,
+                  dict_bits=spec.dict_bits, anchor_bits=spec.anchor_bits, solve_mode=1)
+    blk = MeshCodec(tris, n, n_frames=kf, rank=kb, oi_sweeps=8, **common)
+    one = MeshCodec(tris, n, n_frames=F, rank=spec.rank, oi_sweeps=SWEEPS, **common)
+    pos_d = torch.from_numpy(pos).to(dev)
+    out_b = torch.empty(blk.blocks_size(nb), dtype=torch.uint8, device=dev)
+    out_1 = torch.empty(one.stream_bytes, dtype=torch.uint8, device=dev)
+    rec_b, rec_1 = torch.empty_like(pos_d), torch.empty_like(pos_d)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step_blocks():
+        blk.encode_blocks(pos_d, nb, out=out_b, stream=stream)
+        blk.decode_blocks(out_b, nb, out=rec_b, stream=stream)
+
+    def step_one():
+        one.encode(pos_d, out=out_1, stream=stream)
+        one.decode(out_1, out=rec_1, stream=stream)
+
+    def timed(fn):
+        total = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        return total
+
+    for _ in range(args.warmup):
+        step_blocks()
+        step_one()
+    sampler = ClockSampler()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    ms_b = timed(step_blocks)
+    launches = blk.stats()["launches_encode"] + blk.stats()["launches_decode"]
+    ms_1 = timed(step_one)
+    clocks = sampler.stop()
+    vf = n * F * args.steps
+    value, seconds = aggregate(vf, ms_b / 1e3, world, dist)
+    one_value, _ = aggregate(vf, ms_1 / 1e3, world, dist)
+    r_b = cb.rates(nb, n_vertices=n, n_triangles=tris.shape[0], n_frames=kf, rank=kb, **common)
+    r_1 = cb.rates(1, n_vertices=n, n_triangles=tris.shape[0], n_frames=F, rank=spec.rank,
+                   **common)
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": seconds * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "blocks", "mesh": spec.mesh, "n": n, "F": F, "n_blocks": nb,
+                       "block_frames": kf, "k_per_block": kb, "sweeps_per_block": 8,
+                       "solve_mode": "factored",
+                       "l2": "flushed (256 MiB write) before every step",
+                       "parallelism": f"replicas x{world}"},
+            "nmse": metrics.nmse(pos, rec_b.cpu().numpy()), "rates": r_b,
+            "one_block": {"value": one_value, "k": spec.rank,
+                          "nmse": metrics.nmse(pos, rec_1.cpu().numpy()), "rates": r_1},
+            "clocks": clocks, "gpu_launches": launches, "roofline": None,
+            "cpu_baseline": None, "e2e": None,
+        }
+        print(json.dumps(out), flush=True)
+    blk.close()
+    one.close()
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -693,6 +797,9 @@ def main(argv=None):
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--precision", choices=["fp64", "tf32", "bf16"], default="fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--refine", type=int, default=0,
+                    help="decoder solve by iterative refinement: FP32 CG corrections to "
+                         "10^-r with FP64 residuals (0: off)")
     ap.add_argument("--cg-rtol", type=float, default=None,
                     help="decoder CG tolerance of the learned workload (default 1e-8)")
     ap.add_argument("--solve-mode", choices=["frames", "factored"], default="factored",
@@ -707,6 +814,8 @@ def main(argv=None):
         return run_batched(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "blocks":
+        return run_blocks(args)
     return run_ours(args)
 
 

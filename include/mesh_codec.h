@@ -104,7 +104,12 @@ typedef struct mesh_codec_params {
                                     the decoder's previous dictionary (Section IV, Fig. 6);
                                     0 = every block codes its own dictionary */
     int32_t block_delta_bits;    /* bits per dictionary difference, 0..31 (0 = raw binary64) */
-    int32_t reserved[3];         /* must be zero */
+    int32_t refine;              /* decoder solve: 0 = CG in the precision of the mode;
+                                    r in 1..12 = iterative refinement: the residual of Eq. 12's
+                                    normal equations in FP64, FP32 CG corrections solved to a
+                                    relative 10^-r, until every column's FP64 residual meets
+                                    cg_rtol (FP64 accuracy from FP32 sweeps, any precision) */
+    int32_t reserved[2];         /* must be zero */
 } mesh_codec_params_t;
 
 typedef struct mesh_codec_stats {

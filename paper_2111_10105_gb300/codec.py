@@ -44,7 +44,7 @@ class Params(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("solve_mode", ctypes.c_int32),
         ("oi_refine_sweeps", ctypes.c_int32), ("autotune", ctypes.c_int32),
         ("block_delta", ctypes.c_int32), ("block_delta_bits", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("refine", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
     ]
 
 

@@ -10,6 +10,7 @@
 // Decoder (Eq. 11-12): unpack; delta~ = (U' C')^T; B = L^T delta~ + P^T a^;
 //   Jacobi-CG on (L^T L + P^T P) X = B over all 3F columns; X -> [F][n][3].
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -104,6 +105,11 @@ size_t carve(mesh_codec* h, void* base) {
   h->cg.all_done = c.take<int32_t>(1);
   h->d_status = c.take<uint32_t>(4);
   h->d_match = c.take<int32_t>(1);
+  h->ref_bb = c.take<double>(W);
+  h->ref_rr = c.take<double>(W);
+  h->ref_prev = c.take<double>(W);
+  h->ref_frozen = c.take<int32_t>(W);
+  h->ref_iters = c.take<int32_t>(W);
   size_t off = mixed_carve(h, (char*)base, c.off);
   return off + 1024;
 }
@@ -165,7 +171,8 @@ bool valid_params(const mesh_codec_params_t* p) {
   if (p->autotune != 0 && p->autotune != 1) return false;
   if (p->block_delta != 0 && p->block_delta != 1) return false;
   if (p->block_delta_bits < 0 || p->block_delta_bits > MESH_CODEC_MAX_BITS) return false;
-  for (int i = 0; i < 3; ++i)
+  if (p->refine < 0 || p->refine > 12) return false;
+  for (int i = 0; i < 2; ++i)
     if (p->reserved[i] != 0) return false;
   return true;
 }
@@ -656,7 +663,9 @@ static void decode_prepare(mesh_codec* h, const uint8_t* in, cudaStream_t s, Lau
     if (!d.cached) unit_anchor_columns(h->B, h->dec_anchors, h->n_c, d.Wc, 3 * k, s, L);
   }
   // CG: FP64 vectors, or FP32 vectors with FP64-accurate dot products in the mixed modes
-  d.single = h->lp >= 0 ? 1 : 0;
+  // and for the corrections of the refined solve
+  d.refine = h->p.refine > 0;
+  d.single = (h->lp >= 0 || d.refine) ? 1 : 0;
   d.inv_d = h->inv_d;
   d.inv_diag = h->inv_diag;
   if (d.single) {   // FP32 copies: no FP64 conversions in the FP32 kernels
@@ -675,7 +684,13 @@ static void decode_prepare(mesh_codec* h, const uint8_t* in, cudaStream_t s, Lau
     }
     d.geom = h->tuned;
   }
-  if (x0 && !d.factored) {
+  if (d.refine) {
+    // the refined solve keeps its iterate in FP64 (X), from X0 or zero
+    if (x0 && !d.factored)
+      frames_to_vertex_major(x0, h->X, F, n, s, L);
+    else
+      cudaMemsetAsync(h->X, 0, sizeof(double) * (size_t)n * d.Wc, s);
+  } else if (x0 && !d.factored) {
     // warm start: the caller's X0 [F][n][3] as the CG's first iterate
     frames_to_vertex_major(x0, h->D, F, n, s, L);
     if (d.single)
@@ -750,12 +765,79 @@ static bool decode_cg_chunk(mesh_codec* h, int m, cudaStream_t s, Launches& L) {
   return true;
 }
 
+// Refined solve: outer steps X += D with D the FP32 CG solution of M D = R,
+// R = B - M X formed in FP64, until every column's ||R|| <= cg_rtol ||B||.
+// The inner CG reduces each correction's residual by 10^-refine; the FP32
+// vectors sit in buffers the solve leaves free (X holds the FP64 iterate,
+// Tv and Qv the FP64 products, R / P / D the FP32 vectors).
+static constexpr int kRefineMaxOuter = 30;
+
+static mesh_codec_status_t decode_refine(mesh_codec* h, cudaStream_t s, Launches& L) {
+  DecodeState& d = h->dec;
+  const int n = h->n, W = d.Wc;
+  const long long nw = (long long)n * W;
+  const CgGeom g64 = cg_geometry(n, W);   // the FP64 residual kernels (32 columns per CTA)
+  double* X64 = h->X;
+  double* T64 = h->Tv;
+  double* Rres = h->Qv;
+  float* X32 = (float*)h->R;
+  float* R32 = X32 + nw;
+  float* P32 = (float*)h->P;
+  float* T32 = P32 + nw;
+  float* Q32 = (float*)h->D;
+  const double inner_rtol = std::pow(10.0, -(double)h->p.refine);
+  // the smallest residual binary64 resolves for an iterate X: a multiple of
+  // eps sqrt(n) ||M||_inf ||X|| (||M||_inf <= ||L||_inf ||L||_1 + 1)
+  const double dm = (double)std::max(h->max_degree, 1);
+  const double normM = h->kind == 0 ? 2.0 * (1.0 + dm) + 1.0 : 4.0 * dm * dm + 1.0;
+  const double floor = 100.0 * 0x1.0p-53 * std::sqrt((double)n) * normM;
+  cudaMemsetAsync(h->ref_frozen, 0, sizeof(int32_t) * W, s);
+  cudaMemsetAsync(h->ref_iters, 0, sizeof(int32_t) * W, s);
+  refine_reset(h->ref_prev, W, s, L);
+  refine_col_norms(g64, h->B, h->cg.partials, h->ref_bb, s, L);
+  for (int outer = 0;; ++outer) {
+    refine_residual(g64, h->row_ptr, h->col_idx, h->deg, h->inv_d, h->is_anchor, h->kind, X64,
+                    h->B, T64, Rres, h->ref_frozen, h->cg.partials, h->ref_bb, h->p.cg_rtol,
+                    floor, h->ref_prev, h->ref_rr, h->cg.active, s, L);
+    MC_TRY(cudaMemcpyAsync(h->h_active, h->cg.active, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                           s));
+    MC_TRY(cudaStreamSynchronize(s));
+    if (*h->h_active == 0 || outer == kRefineMaxOuter) break;
+    // FP32 correction (frozen columns have R = 0 and converge at once)
+    // each correction gets at most an eighth of the iteration cap (at least
+    // 1000): a column whose FP32 correction cannot reach the inner tolerance
+    // moves on to the next outer step instead of spinning
+    const int inner_max = std::max(1000, h->p.cg_max_iters / 8);
+    cg_init(d.geom, Rres, X32, R32, P32, d.inv_diag, h->cg, 1, s, L);
+    for (int it = 0; it < inner_max; it += kCgChunk) {
+      const int m = std::min(kCgChunk, inner_max - it);
+      for (int j = 0; j < m; ++j, ++d.it)
+        cg_iteration(d.geom, h->row_ptr, h->col_idx, h->deg, d.inv_d, h->is_anchor, d.inv_diag,
+                     h->kind, X32, R32, P32, T32, Q32, inner_rtol, inner_max, h->cg, 1, s, L,
+                     prof_group(h, d.it));
+      MC_TRY(cudaMemcpyAsync(h->h_active, h->cg.active, sizeof(int32_t),
+                             cudaMemcpyDeviceToHost, s));
+      MC_TRY(cudaStreamSynchronize(s));
+      if (*h->h_active == 0) break;
+    }
+    refine_update(X32, nw, X64, h->cg.iters, W, h->ref_iters, s, L);
+  }
+  // per-column results in the CG state: converged = frozen, iterations, ||R||, ||B||
+  MC_TRY(cudaMemcpyAsync(h->cg.done, h->ref_frozen, sizeof(int32_t) * W,
+                         cudaMemcpyDeviceToDevice, s));
+  MC_TRY(cudaMemcpyAsync(h->cg.iters, h->ref_iters, sizeof(int32_t) * W,
+                         cudaMemcpyDeviceToDevice, s));
+  MC_TRY(cudaMemcpyAsync(h->cg.rr, h->ref_rr, sizeof(double) * W, cudaMemcpyDeviceToDevice, s));
+  MC_TRY(cudaMemcpyAsync(h->cg.bb, h->ref_bb, sizeof(double) * W, cudaMemcpyDeviceToDevice, s));
+  return MC_OK;
+}
+
 // Phase 3: the solution in FP64, the factored combination, the output layout.
 static void decode_finish(mesh_codec* h, double* out, cudaStream_t s, Launches& L) {
   const int n = h->n, F = h->F, k = h->k, W = h->W;
   const DecodeState& d = h->dec;
   const double* Xs = h->X;
-  if (d.single) {   // the mixed modes widen their FP32 iterate into B
+  if (d.single && !d.refine) {   // the mixed modes widen their FP32 iterate into B
     widen((const float*)h->X, (long long)n * d.Wc, h->B, s, L);
     Xs = h->B;
   }
@@ -806,9 +888,14 @@ static mesh_codec_status_t enqueue_decode(mesh_codec* h, const uint8_t* in, doub
                                           const double* dict_ref = nullptr,
                                           const EncodeLayout* lay = nullptr) {
   decode_prepare(h, in, s, L, x0, dict_ref, lay);
-  while (decode_cg_chunk(h, 32, s, L)) {
-    MC_TRY(cudaStreamSynchronize(s));
-    if (*h->h_active == 0) break;
+  if (h->dec.refine) {
+    const mesh_codec_status_t st = decode_refine(h, s, L);
+    if (st != MC_OK) return st;
+  } else {
+    while (decode_cg_chunk(h, 32, s, L)) {
+      MC_TRY(cudaStreamSynchronize(s));
+      if (*h->h_active == 0) break;
+    }
   }
   decode_finish(h, out, s, L);
   return MC_OK;
@@ -1214,6 +1301,11 @@ mesh_codec_status_t mesh_codec_decode_batch(mesh_codec_t* const* handles, int co
     h->launches_decode = 0;
     Launches L{&h->launches_decode};
     decode_prepare(h, bitstreams[i], h->own, L);
+    if (h->dec.refine) {
+      // refined solves synchronise per outer step: run them one by one
+      st[i] = decode_refine(h, h->own, L);
+      continue;
+    }
     active.push_back(i);
   }
   while (!active.empty()) {

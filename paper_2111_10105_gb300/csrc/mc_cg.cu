@@ -582,6 +582,148 @@ CgGeom cg_autotune(int n, int W, const int32_t* row_ptr, const int32_t* col_idx,
   return best;
 }
 
+// ------------------------------------------------ iterative refinement (FP64 residuals)
+// The refined solve keeps X in FP64 and, per outer step, forms the residual
+// R = B - (L^T L + P^T P) X in FP64 (T = L X first), freezes the columns whose
+// ||R|| <= rtol ||B||, and lets an FP32 CG solve M D = R for the others.
+
+// R = B - (L^T T + P^T P X) for unfrozen columns (0 for frozen ones), and the
+// (row block, column) partials of R.R
+__global__ void __launch_bounds__(kCgThreads) k_refine_residual(
+    CgGeom g, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+    const int32_t* __restrict__ deg, const double* __restrict__ inv_d, int kind,
+    const uint8_t* __restrict__ is_anchor, const double* __restrict__ Tv,
+    const double* __restrict__ X, const double* __restrict__ B, double* __restrict__ R,
+    const int32_t* __restrict__ frozen, double* __restrict__ partials) {
+  __shared__ double sh[256];
+  const int col = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int rl = threadIdx.x >> 5;
+  const long long r0 = (long long)blockIdx.y * g.rows_per_block;
+  const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
+  const CsrView v{row_ptr + r0, col_idx};
+  double rr = 0.0, xx = 0.0;
+  if (col < g.W) {
+    const bool fz = frozen[col] != 0;
+    for (long long j = r0 + rl; j < r1; j += 8) {
+      double r = 0.0;
+      if (!fz) {
+        const int b = v.rp[j - r0], e = v.rp[j - r0 + 1];
+        const double acc = (kind == 0) ? gather_wsum(Tv, inv_d, v.ci, b, e, g.W, col)
+                                       : gather_sum(Tv, v.ci, b, e, g.W, col);
+        const double tj = Tv[j * g.W + col];
+        const double xj = X[j * g.W + col];
+        double q = (kind == 0) ? tj - acc : fma((double)deg[j], tj, -acc);
+        if (is_anchor[j]) q += xj;
+        r = B[j * g.W + col] - q;
+        rr = fma(r, r, rr);
+        xx = fma(xj, xj, xx);
+      }
+      R[j * g.W + col] = r;
+    }
+  }
+  cta_col_partial(rr, sh, partials, col, g.W, col < g.W);
+  cta_col_partial(xx, sh, partials + (long long)g.row_blocks * g.W, col, g.W, col < g.W);
+}
+
+// (row block, column) partials of B.B
+__global__ void __launch_bounds__(kCgThreads) k_col_dots(CgGeom g, const double* __restrict__ B,
+                                                         double* __restrict__ partials) {
+  __shared__ double sh[256];
+  const int col = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int rl = threadIdx.x >> 5;
+  const long long r0 = (long long)blockIdx.y * g.rows_per_block;
+  const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
+  double s = 0.0;
+  if (col < g.W)
+    for (long long j = r0 + rl; j < r1; j += 8) {
+      const double b = B[j * g.W + col];
+      s = fma(b, b, s);
+    }
+  cta_col_partial(s, sh, partials, col, g.W, col < g.W);
+}
+
+// out[col] = sum of the partials.  With check (partials of ||R||^2, then of
+// ||X||^2), a column is done when ||R||^2 <= rtol2 ||B||^2, or when an outer
+// step reduced ||R|| by less than half (prev: the last step's ||R||^2) while
+// ||R||^2 <= floor2 ||X||^2: the FP64 residual has reached what binary64 can
+// resolve for that X (backward-error test of mixed-precision refinement);
+// *active counts the columns still open
+__global__ void k_refine_sum(CgGeom g, const double* __restrict__ partials, double* out,
+                             int check, const double* __restrict__ bb, double rtol2,
+                             double floor2, double* prev, int32_t* frozen, int32_t* active) {
+  const int col = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (col >= g.W) return;
+  const double s = warp_col_sum(partials, g.row_blocks, g.W, col);
+  double xx = 0.0;
+  if (check) xx = warp_col_sum(partials + (long long)g.row_blocks * g.W, g.row_blocks, g.W, col);
+  if ((threadIdx.x & 31) == 0) {
+    if (check) {
+      if (!frozen[col]) {
+        out[col] = s;
+        const bool stalled = s > 0.25 * prev[col] && s <= floor2 * xx;
+        if (s <= rtol2 * bb[col] || stalled) frozen[col] = 1;
+        prev[col] = s;
+      }
+      if (!frozen[col]) atomicAdd(active, 1);
+    } else {
+      out[col] = s;
+    }
+  }
+}
+
+__global__ void k_fill_d(double* p, int count, double v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+__global__ void k_refine_add(const float* __restrict__ D, long long count, double* __restrict__ X) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x)
+    X[e] += (double)D[e];
+}
+
+__global__ void k_refine_iters(const int32_t* __restrict__ it, int W, int32_t* total) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < W; c += gridDim.x * blockDim.x)
+    total[c] += it[c];
+}
+
+void refine_col_norms(const CgGeom& g, const double* B, double* partials, double* out,
+                      cudaStream_t s, Launches& L) {
+  dim3 grid((g.W + 31) / 32, g.row_blocks);
+  k_col_dots<<<grid, kCgThreads, 0, s>>>(g, B, partials);
+  k_refine_sum<<<(g.W + 7) / 8, 256, 0, s>>>(g, partials, out, 0, nullptr, 0.0, 0.0, nullptr,
+                                             nullptr, nullptr);
+  L.add(2);
+}
+
+void refine_reset(double* prev, int W, cudaStream_t s, Launches& L) {
+  k_fill_d<<<(W + 255) / 256, 256, 0, s>>>(prev, W, 1e300);
+  L.add(1);
+}
+
+void refine_residual(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx,
+                     const int32_t* deg, const double* inv_d, const uint8_t* is_anchor, int kind,
+                     const double* X, const double* B, double* T, double* R, int32_t* frozen,
+                     double* partials, const double* bb, double rtol, double floor, double* prev,
+                     double* rr, int32_t* active, cudaStream_t s, Launches& L) {
+  dim3 grid((g.W + 31) / 32, g.row_blocks);
+  k_cg_L<double><<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, X, T, frozen);
+  k_refine_residual<<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, is_anchor,
+                                                T, X, B, R, frozen, partials);
+  cudaMemsetAsync(active, 0, sizeof(int32_t), s);
+  k_refine_sum<<<(g.W + 7) / 8, 256, 0, s>>>(g, partials, rr, 1, bb, rtol * rtol, floor * floor,
+                                             prev, frozen, active);
+  L.add(3);
+}
+
+void refine_update(const float* D, long long count, double* X, const int32_t* iters, int W,
+                   int32_t* total, cudaStream_t s, Launches& L) {
+  k_refine_add<<<(int)std::min<long long>((count + 255) / 256, 152 * 16), 256, 0, s>>>(D, count,
+                                                                                      X);
+  k_refine_iters<<<(W + 255) / 256, 256, 0, s>>>(iters, W, total);
+  L.add(2);
+}
+
 // out[e] = (double) X[e]
 __global__ void k_widen(const float* __restrict__ X, long long count, double* __restrict__ out) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;

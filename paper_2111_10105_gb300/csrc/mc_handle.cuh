@@ -11,6 +11,7 @@ struct DecodeState {
   bool factored = false;
   bool cached = false;           // factored solve with the kept anchor response G
   bool store = false;            // this decode computes G and may keep it
+  bool refine = false;           // FP64 residuals with FP32 CG corrections
   int Wc = 0, single = 0, it = 0;
   mc::CgGeom geom{};
   const void* inv_d = nullptr;
@@ -50,6 +51,9 @@ struct mesh_codec {
   int32_t* Gcache_anchors = nullptr;
   bool Gcache_valid = false, Gcache_pending = false;
   int32_t* d_match = nullptr;      // device: anchors differing from the kept set
+  // refined solve: per column ||B||^2, ||R||^2, converged flag, iterations
+  double *ref_bb, *ref_rr, *ref_prev;
+  int32_t *ref_frozen, *ref_iters;
   mc::CgState cg;
   uint32_t* d_status;
   int nnz;

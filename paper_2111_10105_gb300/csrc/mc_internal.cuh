@@ -205,6 +205,22 @@ void cg_iteration(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_id
                   double rtol, int max_iters, CgState& st, int single, cudaStream_t s,
                   Launches& L, cudaEvent_t* ev /* 7 events around the 6 kernels, or null */);
 void widen(const float* X, long long count, double* out, cudaStream_t s, Launches& L);
+// Iterative refinement of the CG solve (FP64 residuals, FP32 corrections):
+// out[col] = ||B_col||^2; the FP64 residual R = B - M X of the unfrozen
+// columns (T = L X as scratch), rr[col] = ||R_col||^2, frozen[col] set where
+// rr <= rtol^2 bb or where the residual stalls below floor * ||X_col|| (prev:
+// the last step's rr, reset to +inf by refine_reset), *active = number still
+// open; X += D and the inner iteration counts added to total.
+void refine_col_norms(const CgGeom& g, const double* B, double* partials, double* out,
+                      cudaStream_t s, Launches& L);
+void refine_reset(double* prev, int W, cudaStream_t s, Launches& L);
+void refine_residual(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx,
+                     const int32_t* deg, const double* inv_d, const uint8_t* is_anchor, int kind,
+                     const double* X, const double* B, double* T, double* R, int32_t* frozen,
+                     double* partials, const double* bb, double rtol, double floor, double* prev,
+                     double* rr, int32_t* active, cudaStream_t s, Launches& L);
+void refine_update(const float* D, long long count, double* X, const int32_t* iters, int W,
+                   int32_t* total, cudaStream_t s, Launches& L);
 // CG start from the X already in place (warm start), T and Q as scratch
 void cg_init_warm(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx,
                   const int32_t* deg, const void* inv_d, const uint8_t* is_anchor, int kind,
