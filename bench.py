@@ -53,6 +53,15 @@ LEARNED_OI_CAP = 100
 LEARNED_FIELDS = 16          # learned workload motion: 16 fields,
 LEARNED_CYCLES = 8           # [0.5, 3] x 8 cycles per 300-frame segment
 LEARNED_CG_RTOL = 1e-8
+# DRAM bytes (read + write) per launch from ncu captures of exactly these
+# configurations (workload, precision, refine, CG columns, kernel), with the
+# profiles/ summary they come from; a kernel changed since is to be removed
+MEASURED_TRAFFIC = {
+    ("torus200x100_F256_k32", "fp64", 0, 96, "k_cg_LT"):
+        (31.56e6, "profiles/k_cg_L_LT_torus200x100_F256_k32_fp64.md"),
+    ("torus200x100_F256_k32", "fp64", 0, 96, "k_cg_L"):
+        (16.11e6, "profiles/k_cg_L_LT_torus200x100_F256_k32_fp64.md"),
+}
 
 
 # ---------------------------------------------------------------- helpers
@@ -380,6 +389,11 @@ def run_ours(args):
     nnz = int(mc.buffer(1).numel())
     cols = stats["cg_columns"]
     rl = roofline(profile, stats, n, cols, nnz, spec.n_anchors, peaks, single)
+    measured = MEASURED_TRAFFIC.get((args.workload, args.precision, args.refine, cols,
+                                     rl["kernel"]))
+    if measured:
+        rl["traffic"] = measured[0]
+        rl["traffic_source"] = measured[1]
 
     if rank == 0:
         out = {
