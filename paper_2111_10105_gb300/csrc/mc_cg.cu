@@ -14,7 +14,7 @@
 //   5. beta, convergence, active count  (per column, fixed-order reduction)
 //   6. P = D^-1 R + beta P
 // Dot products are reduced deterministically: per (row block, column)
-// partials in a fixed order, then one warp per column with a fixed shuffle
+// partials in a fixed order, then one CTA per column with a fixed reduction
 // tree.  A converged column is frozen (alpha = beta = 0, no more updates),
 // so its result does not depend on the other columns.
 #include <algorithm>
@@ -137,25 +137,32 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_init(CgGeom g, const double* 
   cta_col_partial(bb.value(), sh, partials + plane, col, g.W, valid);
 }
 
-// one warp per column: fixed-order sum of the row-block partials
-__device__ __forceinline__ double warp_col_sum(const double* part, int row_blocks, int W,
-                                               int col) {
-  const int lane = threadIdx.x & 31;
+// One CTA (256 threads) per column: fixed-order sum of the row-block partials
+// (a strided sum per thread, a shuffle tree per warp, then the 8 warps in
+// order); the result is valid in thread 0.  A whole CTA per column keeps
+// many loads in flight where one warp per column was latency-bound.
+__device__ __forceinline__ double col_sum(const double* part, int row_blocks, int W, int col) {
+  __shared__ double sh[8];
   double s = 0.0;
-  for (int b = lane; b < row_blocks; b += 32) s += part[(long long)b * W + col];
+  for (int b = threadIdx.x; b < row_blocks; b += 256) s += part[(long long)b * W + col];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  return s;  // valid in lane 0
+  __syncthreads();   // thread 0 has read the previous call's sums
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < 8; ++w) t += sh[w];
+  return t;
 }
 
 __global__ void k_cg_init_cols(CgGeom g, const double* __restrict__ partials, double* rz,
                                double* bb, int32_t* done, int32_t* iters) {
-  const int col = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (col >= g.W) return;
+  const int col = blockIdx.x;   // grid: one CTA per column
   const long long plane = (long long)g.row_blocks * g.W;
-  double a = warp_col_sum(partials, g.row_blocks, g.W, col);
-  double b = warp_col_sum(partials + plane, g.row_blocks, g.W, col);
-  if ((threadIdx.x & 31) == 0) {
+  double a = col_sum(partials, g.row_blocks, g.W, col);
+  double b = col_sum(partials + plane, g.row_blocks, g.W, col);
+  if (threadIdx.x == 0) {
     rz[col] = a;
     bb[col] = b;
     done[col] = (b == 0.0) ? 1 : 0;
@@ -273,10 +280,9 @@ __global__ void k_cg_alpha(CgGeom g, const double* __restrict__ partials,
                            const double* __restrict__ rz, double* alpha,
                            const int32_t* __restrict__ done, int32_t* active) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *active = 0;
-  const int col = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (col >= g.W) return;
-  double pap = warp_col_sum(partials, g.row_blocks, g.W, col);
-  if ((threadIdx.x & 31) == 0) {
+  const int col = blockIdx.x;   // grid: one CTA per column
+  double pap = col_sum(partials, g.row_blocks, g.W, col);
+  if (threadIdx.x == 0) {
     double a = 0.0;
     if (!done[col] && pap > 0.0) a = rz[col] / pap;
     alpha[col] = a;
@@ -320,12 +326,11 @@ __global__ void k_cg_beta(CgGeom g, const double* __restrict__ partials, double*
                           double* rr_out, const double* __restrict__ bb, double* beta,
                           int32_t* done, int32_t* iters, double rtol2, int max_iters,
                           int32_t* active) {
-  const int col = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (col >= g.W) return;
+  const int col = blockIdx.x;   // grid: one CTA per column
   const long long plane = (long long)g.row_blocks * g.W;
-  double rzn = warp_col_sum(partials, g.row_blocks, g.W, col);
-  double rr = warp_col_sum(partials + plane, g.row_blocks, g.W, col);
-  if ((threadIdx.x & 31) == 0) {
+  double rzn = col_sum(partials, g.row_blocks, g.W, col);
+  double rr = col_sum(partials + plane, g.row_blocks, g.W, col);
+  if (threadIdx.x == 0) {
     if (done[col]) {
       beta[col] = 0.0;
       return;
@@ -371,7 +376,7 @@ static void cg_init_t(const CgGeom& g, const double* B, void* X, void* R, void* 
   dim3 grid((g.W + 31) / 32, g.row_blocks);
   k_cg_init<T><<<grid, kCgThreads, 0, s>>>(g, B, (T*)X, (T*)R, (T*)P, (const T*)inv_diag,
                                            st.partials);
-  k_cg_init_cols<<<(g.W + 7) / 8, 256, 0, s>>>(g, st.partials, st.rz, st.bb, st.done, st.iters);
+  k_cg_init_cols<<<g.W, 256, 0, s>>>(g, st.partials, st.rz, st.bb, st.done, st.iters);
   L.add(2);
 }
 
@@ -420,7 +425,7 @@ static void cg_init_warm_t(const CgGeom& g, const int32_t* row_ptr, const int32_
   k_cg_LT<T><<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, is_anchor, Tv, X,
                                           Q, st.done, st.partials);
   k_cg_init_warm<T><<<grid, kCgThreads, 0, s>>>(g, B, Q, R, P, inv_diag, st.partials);
-  k_cg_init_cols<<<(g.W + 7) / 8, 256, 0, s>>>(g, st.partials, st.rz, st.bb, st.done, st.iters);
+  k_cg_init_cols<<<g.W, 256, 0, s>>>(g, st.partials, st.rz, st.bb, st.done, st.iters);
   L.add(4);
 }
 
@@ -442,7 +447,7 @@ void cg_init(const CgGeom& g, const double* B, void* X, void* R, void* P,
              const void* inv_diag, CgState& st, int single, cudaStream_t s, Launches& L) {
   if (cg4_applies(g.W, single)) {
     cg4_init(g, B, (float*)X, (float*)R, (float*)P, (const float*)inv_diag, st.partials, s);
-    k_cg_init_cols<<<(g.W + 7) / 8, 256, 0, s>>>(g, st.partials, st.rz, st.bb, st.done,
+    k_cg_init_cols<<<g.W, 256, 0, s>>>(g, st.partials, st.rz, st.bb, st.done,
                                                  st.iters);
     L.add(2);
   } else if (single) {
@@ -458,7 +463,7 @@ static void cg_iteration4(const CgGeom& g, const int32_t* row_ptr, const int32_t
                           const float* inv_diag, int kind, float* X, float* R, float* P,
                           float* Tv, float* Q, double rtol, int max_iters, CgState& st,
                           cudaStream_t s, Launches& L, cudaEvent_t* ev) {
-  dim3 cgrid((g.W + 7) / 8);
+  dim3 cgrid(g.W);
   if (ev) cudaEventRecord(ev[0], s);
   cg4_op(g, row_ptr, col_idx, deg, inv_d, kind, is_anchor, P, Tv, Q, st.done, st.partials, s, ev);
   if (ev) cudaEventRecord(ev[2], s);
@@ -481,7 +486,7 @@ static void cg_iteration_t(const CgGeom& g, const int32_t* row_ptr, const int32_
                            double rtol, int max_iters, CgState& st, cudaStream_t s, Launches& L,
                            cudaEvent_t* ev) {
   dim3 grid((g.W + 31) / 32, g.row_blocks);
-  dim3 cgrid((g.W + 7) / 8);
+  dim3 cgrid(g.W);
   if (ev) cudaEventRecord(ev[0], s);
   k_cg_L<T><<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, P, Tv, st.done);
   if (ev) cudaEventRecord(ev[1], s);
@@ -651,12 +656,11 @@ __global__ void __launch_bounds__(kCgThreads) k_col_dots(CgGeom g, const double*
 __global__ void k_refine_sum(CgGeom g, const double* __restrict__ partials, double* out,
                              int check, const double* __restrict__ bb, double rtol2,
                              double floor2, double* prev, int32_t* frozen, int32_t* active) {
-  const int col = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (col >= g.W) return;
-  const double s = warp_col_sum(partials, g.row_blocks, g.W, col);
+  const int col = blockIdx.x;   // grid: one CTA per column
+  const double s = col_sum(partials, g.row_blocks, g.W, col);
   double xx = 0.0;
-  if (check) xx = warp_col_sum(partials + (long long)g.row_blocks * g.W, g.row_blocks, g.W, col);
-  if ((threadIdx.x & 31) == 0) {
+  if (check) xx = col_sum(partials + (long long)g.row_blocks * g.W, g.row_blocks, g.W, col);
+  if (threadIdx.x == 0) {
     if (check) {
       if (!frozen[col]) {
         out[col] = s;
@@ -691,7 +695,7 @@ void refine_col_norms(const CgGeom& g, const double* B, double* partials, double
                       cudaStream_t s, Launches& L) {
   dim3 grid((g.W + 31) / 32, g.row_blocks);
   k_col_dots<<<grid, kCgThreads, 0, s>>>(g, B, partials);
-  k_refine_sum<<<(g.W + 7) / 8, 256, 0, s>>>(g, partials, out, 0, nullptr, 0.0, 0.0, nullptr,
+  k_refine_sum<<<g.W, 256, 0, s>>>(g, partials, out, 0, nullptr, 0.0, 0.0, nullptr,
                                              nullptr, nullptr);
   L.add(2);
 }
@@ -711,7 +715,7 @@ void refine_residual(const CgGeom& g, const int32_t* row_ptr, const int32_t* col
   k_refine_residual<<<grid, kCgThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, is_anchor,
                                                 T, X, B, R, frozen, partials);
   cudaMemsetAsync(active, 0, sizeof(int32_t), s);
-  k_refine_sum<<<(g.W + 7) / 8, 256, 0, s>>>(g, partials, rr, 1, bb, rtol * rtol, floor * floor,
+  k_refine_sum<<<g.W, 256, 0, s>>>(g, partials, rr, 1, bb, rtol * rtol, floor * floor,
                                              prev, frozen, active);
   L.add(3);
 }
