@@ -628,6 +628,89 @@ def run_blocks(args):
     return 0
 
 
+def run_rd(args):
+    """Rate-distortion sweep on the torus sequence (20,000 vertices, 256
+    frames, FP64, factored solve): NMSE against the bits per vertex and frame
+    (Eq. 13's q_s and the stream's own rate) for k in {8, 16, 32, 64} and
+    coefficient bits in {8, 10, 12, 14} (the question of Fig. 3: how many
+    rows k_l are worth coding).  `value` is the throughput of the default
+    point (k 32, 12 bits); every point is timed over `steps` encode + decode
+    steps after `warmup` untimed ones."""
+    import torch
+
+    from oracle import metrics
+    from paper_2111_10105_gb300 import MeshCodec, codec as cb
+    from synth import make_sequence, config_spec
+
+    world, rank, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = config_spec(DEFAULT_WORKLOAD)
+    tris, pos = make_sequence(spec)
+    F, n = pos.shape[0], pos.shape[1]
+    pos_d = torch.from_numpy(pos).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    points, value, launches = [], None, 0
+    sampler = ClockSampler()
+    sampler.start()
+    for k in (8, 16, 32, 64):
+        for bits in (8, 10, 12, 14):
+            kw = dict(n_frames=F, rank=k, n_anchors=spec.n_anchors, seed=spec.seed,
+                      coeff_bits=bits, dict_bits=spec.dict_bits, anchor_bits=spec.anchor_bits,
+                      oi_sweeps=SWEEPS, solve_mode=1)
+            with MeshCodec(tris, n, **kw) as mc:
+                out = torch.empty(mc.stream_bytes, dtype=torch.uint8, device=dev)
+                rec = torch.empty_like(pos_d)
+                for _ in range(args.warmup):
+                    mc.encode(pos_d, out=out, stream=stream)
+                    mc.decode(out, out=rec, stream=stream)
+                ms = 0.0
+                for _ in range(args.steps):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    mc.encode(pos_d, out=out, stream=stream)
+                    mc.decode(out, out=rec, stream=stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms += e0.elapsed_time(e1)
+                st = mc.stats()
+                launches += st["launches_encode"] + st["launches_decode"]
+                r = cb.rates(1, n_vertices=n, n_triangles=tris.shape[0], **kw)
+                vfs = n * F * args.steps / (ms / 1e3)
+                points.append({"k": k, "coeff_bits": bits, "q_s": r["q_s"],
+                               "stream_bpvf": r["stream"],
+                               "nmse": metrics.nmse(pos, rec.cpu().numpy()),
+                               "vertex_frames_per_s": vfs, "cg_iters_mean": st["cg_iters_mean"]})
+                if k == spec.rank and bits == spec.coeff_bits:
+                    value = vfs
+    clocks = sampler.stop()
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": n * F / value * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "rd", "mesh": spec.mesh, "n": n, "F": F,
+                       "k": [8, 16, 32, 64], "coeff_bits": [8, 10, 12, 14],
+                       "l2": "flushed (256 MiB write) before every step",
+                       "parallelism": f"replicas x{world}"},
+            "points": points, "clocks": clocks, "gpu_launches": launches, "roofline": None,
+            "cpu_baseline": None, "e2e": None,
+        }
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def run_learned(args):
     """The 512x512 grid (262,144 vertices, F = 300 per segment, k = 64, 2,621
     anchors) as one coherent sequence coded segment by segment.  Each timed
@@ -830,6 +913,8 @@ def main(argv=None):
         return run_learned(args)
     if args.workload == "blocks":
         return run_blocks(args)
+    if args.workload == "rd":
+        return run_rd(args)
     return run_ours(args)
 
 
