@@ -342,9 +342,12 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_copy_buffer(const mesh_codec_t* h,
                                            void* dst, size_t count, void* stream);
 
 /* Kernel timing.  With `every` > 0, each decode records CUDA events on its
- * stream around the kernels of every `every`-th CG iteration and adds their
- * durations to per-kernel totals; 0 turns it off.  Either call resets the
- * totals.  mesh_codec_get_profile synchronises the handle's last stream. */
+ * stream around the kernels of sampled CG iterations and adds their
+ * durations to per-kernel totals; 0 turns it off.  Full runs of 32
+ * iterations sample their first one (the other 31 replay from a CUDA graph,
+ * as without timing); shorter runs sample every `every`-th iteration.
+ * Either call resets the totals.  mesh_codec_get_profile synchronises the
+ * handle's last stream. */
 #define MESH_CODEC_PROF_KERNELS 8
 typedef struct mesh_codec_profile {
     int32_t n_kernels;

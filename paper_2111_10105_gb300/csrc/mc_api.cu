@@ -231,7 +231,8 @@ void mesh_codec_destroy(mesh_codec_t* h) {
   if (h->ev_done) cudaEventDestroy(h->ev_done);
   if (h->ev_chunk) cudaEventDestroy(h->ev_chunk);
   if (h->own) cudaStreamDestroy(h->own);
-  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  for (cudaGraphExec_t g : h->graph_exec)
+    if (g) cudaGraphExecDestroy(g);
   if (h->cap) cudaStreamDestroy(h->cap);
   delete h;
 }
@@ -711,21 +712,24 @@ static void decode_prepare(mesh_codec* h, const uint8_t* in, cudaStream_t s, Lau
 // iteration cap has been reached.
 // A full chunk of CG iterations is replayed from a CUDA graph captured once
 // per (column count, precision, tile shape): one launch instead of six per
-// iteration.  Kernel timing (mesh_codec_set_profiling) uses direct launches.
+// iteration.  With kernel timing on (mesh_codec_set_profiling) the chunk's
+// first iteration runs as direct launches between CUDA events and the other
+// kCgChunk - 1 come from a second graph, so timing samples one iteration in
+// kCgChunk without giving up the graph replay.
 static constexpr int kCgChunk = 32;
 
-static bool chunk_graph(mesh_codec* h) {
+static bool chunk_graph(mesh_codec* h, int slot, int len) {
   const DecodeState& d = h->dec;
-  if (h->graph_exec && h->graph_W == d.Wc && h->graph_single == d.single &&
-      h->graph_rpb == d.geom.rows_per_block)
+  if (h->graph_exec[slot] && h->graph_W[slot] == d.Wc && h->graph_single[slot] == d.single &&
+      h->graph_rpb[slot] == d.geom.rows_per_block)
     return true;
-  if (h->graph_exec) {
-    cudaGraphExecDestroy(h->graph_exec);
-    h->graph_exec = nullptr;
+  if (h->graph_exec[slot]) {
+    cudaGraphExecDestroy(h->graph_exec[slot]);
+    h->graph_exec[slot] = nullptr;
   }
   if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
   Launches none{nullptr};
-  for (int j = 0; j < kCgChunk; ++j)
+  for (int j = 0; j < len; ++j)
     cg_iteration(d.geom, h->row_ptr, h->col_idx, h->deg, d.inv_d, h->is_anchor, d.inv_diag,
                  h->kind, h->X, h->R, h->P, h->Tv, h->Qv, h->p.cg_rtol, h->p.cg_max_iters, h->cg,
                  d.single, h->cap, none, nullptr);
@@ -734,16 +738,16 @@ static bool chunk_graph(mesh_codec* h) {
     cudaGetLastError();
     return false;
   }
-  cudaError_t e = cudaGraphInstantiate(&h->graph_exec, g, 0);
+  cudaError_t e = cudaGraphInstantiate(&h->graph_exec[slot], g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
-    h->graph_exec = nullptr;
+    h->graph_exec[slot] = nullptr;
     cudaGetLastError();
     return false;
   }
-  h->graph_W = d.Wc;
-  h->graph_single = d.single;
-  h->graph_rpb = d.geom.rows_per_block;
+  h->graph_W[slot] = d.Wc;
+  h->graph_single[slot] = d.single;
+  h->graph_rpb[slot] = d.geom.rows_per_block;
   return true;
 }
 
@@ -751,9 +755,15 @@ static bool decode_cg_chunk(mesh_codec* h, int m, cudaStream_t s, Launches& L) {
   DecodeState& d = h->dec;
   m = std::min(m, h->p.cg_max_iters - d.it);
   if (m <= 0) return false;
-  if (m == kCgChunk && h->prof_every == 0 && chunk_graph(h)) {
-    cudaGraphLaunch(h->graph_exec, s);
+  if (m == kCgChunk && h->prof_every == 0 && chunk_graph(h, 0, kCgChunk)) {
+    cudaGraphLaunch(h->graph_exec[0], s);
     L.add(6 * kCgChunk);
+  } else if (m == kCgChunk && h->prof_every > 0 && chunk_graph(h, 1, kCgChunk - 1)) {
+    cg_iteration(d.geom, h->row_ptr, h->col_idx, h->deg, d.inv_d, h->is_anchor, d.inv_diag,
+                 h->kind, h->X, h->R, h->P, h->Tv, h->Qv, h->p.cg_rtol, h->p.cg_max_iters, h->cg,
+                 d.single, s, L, prof_group(h, d.it));
+    cudaGraphLaunch(h->graph_exec[1], s);
+    L.add(6 * (kCgChunk - 1));
   } else {
     for (int j = 0; j < m; ++j)
       cg_iteration(d.geom, h->row_ptr, h->col_idx, h->deg, d.inv_d, h->is_anchor, d.inv_diag,

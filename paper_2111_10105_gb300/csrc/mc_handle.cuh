@@ -95,8 +95,9 @@ struct mesh_codec {
   int tuned_W = -1, tuned_single = -1;
   cudaStream_t own = nullptr;
   cudaStream_t cap = nullptr;              // capture stream for the CG chunk graph
-  cudaGraphExec_t graph_exec = nullptr;    // kCgChunk CG iterations
-  int graph_W = -1, graph_single = -1, graph_rpb = -1;
+  // kCgChunk CG iterations [0], and kCgChunk - 1 after a timed one [1]
+  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+  int graph_W[2] = {-1, -1}, graph_single[2] = {-1, -1}, graph_rpb[2] = {-1, -1};
   cudaEvent_t ev_fork = nullptr, ev_done = nullptr, ev_chunk = nullptr;
 };
 
