@@ -685,6 +685,12 @@ static void decode_prepare(mesh_codec* h, const uint8_t* in, cudaStream_t s, Lau
     }
     d.geom = h->tuned;
   }
+  {
+    // the FP32 operator kernels stage each row block's CSR slice in shared
+    // memory when it fits a modest budget (12 KB)
+    const long long cap = (long long)d.geom.rows_per_block * std::max(h->max_degree, 1);
+    d.geom.csr_cap = (cap + d.geom.rows_per_block + 1) * 4 <= 12 * 1024 ? (int)cap : 0;
+  }
   if (d.refine) {
     // the refined solve keeps its iterate in FP64 (X), from X0 or zero
     if (x0 && !d.factored)

@@ -151,6 +151,35 @@ __device__ __forceinline__ float4 wgather4(const float* __restrict__ V, const fl
   return acc;
 }
 
+// The CTA's slice of the adjacency, staged in shared memory when the tile
+// geometry allows it (g.csr_cap > 0): row offsets relative to the block's
+// first entry, then the column indices.  All threads of the CTA take part.
+// Each gather then finds its neighbour indices in shared memory instead of
+// behind two dependent global loads.  rp is indexed by row - r0.
+struct CsrSlice {
+  const int32_t* rp;
+  const int32_t* ci;
+};
+
+__device__ __forceinline__ CsrSlice stage_csr(const CgGeom& g, const int32_t* __restrict__ row_ptr,
+                                              const int32_t* __restrict__ col_idx, long long r0,
+                                              long long r1, int32_t* smem) {
+  if (g.csr_cap > 0) {
+    const int base = row_ptr[r0];
+    const int cnt = row_ptr[r1] - base;
+    if (cnt <= g.csr_cap) {                 // the same for every thread of the CTA
+      int32_t* s_rp = smem;
+      int32_t* s_ci = smem + g.rows_per_block + 1;
+      const int nr = (int)(r1 - r0);
+      for (int t = threadIdx.x; t <= nr; t += blockDim.x) s_rp[t] = row_ptr[r0 + t] - base;
+      for (int t = threadIdx.x; t < cnt; t += blockDim.x) s_ci[t] = col_idx[base + t];
+      __syncthreads();
+      return CsrSlice{s_rp, s_ci};
+    }
+  }
+  return CsrSlice{row_ptr + r0, col_idx};
+}
+
 __global__ void __launch_bounds__(kThreads) k4_L(CgGeom g, const int32_t* __restrict__ row_ptr,
                                                  const int32_t* __restrict__ col_idx,
                                                  const int32_t* __restrict__ deg,
@@ -158,13 +187,15 @@ __global__ void __launch_bounds__(kThreads) k4_L(CgGeom g, const int32_t* __rest
                                                  const float* __restrict__ P,
                                                  float* __restrict__ T,
                                                  const int32_t* __restrict__ done) {
+  extern __shared__ int32_t smem_csr[];
   const int col0 = blockIdx.x * kCols + (threadIdx.x & 31) * 4;
   const int rl = threadIdx.x >> 5;
-  if (col0 >= g.W || group_done(done, col0)) return;
   const long long r0 = (long long)blockIdx.y * g.rows_per_block;
   const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
+  const CsrSlice cs = stage_csr(g, row_ptr, col_idx, r0, r1, smem_csr);
+  if (col0 >= g.W || group_done(done, col0)) return;
   for (long long i = r0 + rl; i < r1; i += 8) {
-    const float4 s = gather4(P, col_idx, row_ptr[i], row_ptr[i + 1], g.W, col0);
+    const float4 s = gather4(P, cs.ci, cs.rp[i - r0], cs.rp[i - r0 + 1], g.W, col0);
     const float4 p = ld4(P + i * g.W + col0);
     float4 t;
     if (kind == 0) {
@@ -189,6 +220,9 @@ __global__ void __launch_bounds__(kThreads) k4_LT(CgGeom g, const int32_t* __res
                                                   float* __restrict__ Q,
                                                   const int32_t* __restrict__ done,
                                                   double* __restrict__ partials) {
+  // (the CSR slice stays in global memory here: staging it costs this kernel
+  // four registers and an occupancy step, more than the shorter load chain
+  // saves; measured on the 99,856-vertex grid)
   __shared__ double sh[8][kCols + 1];
   const int col0 = blockIdx.x * kCols + (threadIdx.x & 31) * 4;
   const int rl = threadIdx.x >> 5;
@@ -305,7 +339,8 @@ void cg4_op(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx, con
             const float* inv_d, int kind, const uint8_t* is_anchor, const float* P, float* T,
             float* Q, const int32_t* done, double* partials, cudaStream_t s, cudaEvent_t* ev) {
   dim3 grid((g.W + kCols - 1) / kCols, g.row_blocks);
-  k4_L<<<grid, kThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, P, T, done);
+  const size_t smem = g.csr_cap > 0 ? sizeof(int32_t) * (g.rows_per_block + 1 + g.csr_cap) : 0;
+  k4_L<<<grid, kThreads, smem, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, P, T, done);
   if (ev) cudaEventRecord(ev[1], s);
   k4_LT<<<grid, kThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, is_anchor, T, P, Q,
                                   done, partials);

@@ -187,6 +187,10 @@ struct CgState {
 };
 struct CgGeom {
   int n, W, row_blocks, rows_per_block;
+  // adjacency entries one row block can hold (rows_per_block x the largest
+  // degree): the FP32 operator kernels stage their block's CSR slice in shared
+  // memory when it is set; 0 reads the CSR from global memory
+  int csr_cap;
 };
 CgGeom cg_geometry(int n, int W);
 CgGeom cg_geometry_rows(int n, int W, int rows_per_block);
