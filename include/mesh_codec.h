@@ -75,7 +75,11 @@ typedef enum mesh_codec_solve_mode {
                                     the order of Eq. 11-12 */
     MC_SOLVE_FACTORED = 1,       /* 3k + n_c columns: M Y = L^T C'^T and M G = P^T, then
                                     X_c = Y_c U_c'^T + G a^_c (same solution, reassociated) */
-    MC_SOLVE_AUTO = 2            /* FACTORED when 3k + n_c < 3F, else FRAMES */
+    MC_SOLVE_AUTO = 2            /* FACTORED when 3k + n_c < 3F, or when the stream's
+                                    anchors repeat the previous decode's (its anchor
+                                    response G is then kept, and later decodes with
+                                    those anchors solve 3k columns); else FRAMES.
+                                    A decode given a first iterate keeps the first rule */
 } mesh_codec_solve_mode_t;
 
 typedef struct mesh_codec_params {

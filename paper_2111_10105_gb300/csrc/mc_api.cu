@@ -623,18 +623,43 @@ static void decode_prepare(mesh_codec* h, const uint8_t* in, cudaStream_t s, Lau
   vertex_scalars_marked(h->row_ptr, h->col_idx, h->deg, h->is_anchor, n, h->kind, h->inv_d,
                         h->inv_diag, s, L);
   d.factored = use_factored(h);
-  // the kept anchor response applies when this stream's anchors are its anchors
+  // the kept anchor response applies when this stream's anchors are its
+  // anchors; in the automatic mode, anchors that repeat the previous decode's
+  // make the factored solve worth its extra n_c columns once (its G then
+  // serves every later decode), unless a first iterate asks for the frames solve
+  const bool automatic = h->p.solve_mode == MC_SOLVE_AUTO && x0 == nullptr;
   d.cached = false;
-  if (d.factored && h->Gcache_valid) {
+  bool repeat = false;
+  if (h->n_c > 0 && ((d.factored && h->Gcache_valid) || (automatic && h->anchors_kept))) {
     cudaMemsetAsync(h->d_match, 0, sizeof(int32_t), s);
     k_count_mismatch<<<(h->n_c + 255) / 256, 256, 0, s>>>(h->dec_anchors, h->Gcache_anchors,
                                                           h->n_c, h->d_match);
     L.add(1);
     cudaMemcpyAsync(h->h_active + 1, h->d_match, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
-    d.cached = h->h_active[1] == 0;
+    repeat = h->h_active[1] == 0;
+  }
+  if (repeat && h->Gcache_valid) {
+    d.factored = true;
+    d.cached = true;
+  } else if (repeat && automatic) {
+    d.factored = true;
   }
   d.store = d.factored && !d.cached;
+  if (automatic && !d.factored && h->n_c > 0) {
+    // keep this decode's anchors (a G kept for other anchors no longer applies)
+    if (!h->Gcache_anchors &&
+        cudaMalloc(&h->Gcache_anchors, sizeof(int32_t) * h->n_c) != cudaSuccess) {
+      cudaGetLastError();
+      h->Gcache_anchors = nullptr;
+    }
+    if (h->Gcache_anchors) {
+      cudaMemcpyAsync(h->Gcache_anchors, h->dec_anchors, sizeof(int32_t) * h->n_c,
+                      cudaMemcpyDeviceToDevice, s);
+      h->Gcache_valid = false;
+      h->anchors_kept = true;
+    }
+  }
   // CG columns: 3F frames (Eq. 11-12 as written), or 3k + n_c factored columns,
   // or the 3k data columns with the kept anchor response (the FP32 factored
   // solve pads its column count to a multiple of 4 with zero right-hand
@@ -872,14 +897,15 @@ static void decode_finish(mesh_codec* h, double* out, cudaStream_t s, Launches& 
     vertex_major_to_frames(h->D, out, F, n, s, L);
     if (d.store) {
       // keep G and its anchors; valid once the decode reports every column converged
-      if (!h->Gcache) {
-        if (cudaMalloc(&h->Gcache, sizeof(double) * (size_t)n * h->n_c) != cudaSuccess ||
-            cudaMalloc(&h->Gcache_anchors, sizeof(int32_t) * h->n_c) != cudaSuccess) {
-          cudaGetLastError();
-          if (h->Gcache) cudaFree(h->Gcache);
-          h->Gcache = nullptr;
-          h->Gcache_anchors = nullptr;
-        }
+      if (!h->Gcache_anchors &&
+          cudaMalloc(&h->Gcache_anchors, sizeof(int32_t) * h->n_c) != cudaSuccess) {
+        cudaGetLastError();
+        h->Gcache_anchors = nullptr;
+      }
+      if (!h->Gcache && h->Gcache_anchors &&
+          cudaMalloc(&h->Gcache, sizeof(double) * (size_t)n * h->n_c) != cudaSuccess) {
+        cudaGetLastError();
+        h->Gcache = nullptr;
       }
       if (h->Gcache) {
         h->Gcache_valid = false;
@@ -890,6 +916,7 @@ static void decode_finish(mesh_codec* h, double* out, cudaStream_t s, Launches& 
                         cudaMemcpyDeviceToDevice, s);
         L.add(1);
         h->Gcache_pending = true;
+        h->anchors_kept = true;
       }
     }
   }

@@ -46,10 +46,13 @@ struct mesh_codec {
   // depends only on the connectivity and the anchor set, so the handle keeps
   // the G of its last complete factored decode (own allocation, made on first
   // use) together with that decode's anchors, and later decodes with the
-  // same anchors solve only the 3k data columns.
+  // same anchors solve only the 3k data columns.  Gcache_anchors holds the
+  // anchors of the latest decode (anchors_kept), with or without a G for them:
+  // in the automatic solve mode a repeated anchor set switches a frames
+  // decode to the factored one, whose G every later decode then reuses.
   double* Gcache = nullptr;
   int32_t* Gcache_anchors = nullptr;
-  bool Gcache_valid = false, Gcache_pending = false;
+  bool Gcache_valid = false, Gcache_pending = false, anchors_kept = false;
   int32_t* d_match = nullptr;      // device: anchors differing from the kept set
   // refined solve: per column ||B||^2, ||R||^2, converged flag, iterations
   double *ref_bb, *ref_rr, *ref_prev;

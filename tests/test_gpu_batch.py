@@ -50,7 +50,10 @@ def test_batch_equals_single_and_oracle():
     cs = _codecs(seqs)
     bits = encode_batch(cs, pos_d)
     recs = decode_batch(cs, bits)
-    for c, b, r, (tris, pos), spec in zip(cs, bits, recs, seqs, SPECS):
+    # fresh handles for the single calls: a handle's later decodes may take
+    # another (equal up to rounding) solve path once its anchors repeat
+    singles = _codecs(seqs)
+    for c, b, r, (tris, pos), spec in zip(singles, bits, recs, seqs, SPECS):
         b1 = c.encode(torch.from_numpy(pos).cuda())
         assert torch.equal(b1, b)
         r1 = c.decode(b1)
@@ -59,7 +62,7 @@ def test_batch_equals_single_and_oracle():
                       seed=spec.seed, oi_sweeps=25)
         e_o = metrics.nmse(pos, oc.decode(oc.encode(tris, pos, p), tris))
         assert abs(metrics.nmse(pos, r.cpu().numpy()) - e_o) <= 1e-8 * e_o
-    for c in cs:
+    for c in cs + singles:
         c.close()
 
 
