@@ -4,10 +4,15 @@
 // mc_cg.cu, for column counts W divisible by 4: every load and store moves a
 // float4 (512 bytes per warp per vertex row instead of 128), which keeps
 // enough bytes in flight per SM for these HBM-bound sweeps.  A CTA covers
-// 128 columns x 8 row lanes.  A group of four columns is skipped only when
-// all four have converged; a converged column inside an active group is
-// recomputed harmlessly (its alpha and beta are 0, its dot products unused).
+// LANES column lanes (4 * LANES columns) x 8 row lanes, LANES = 32, 16 or 8
+// (256, 128 or 64 threads), chosen per column count to leave the fewest
+// columns idle: each column keeps the same row lanes and the same fixed
+// reduction order at every width, so the width does not change the results.
+// A group of four columns is skipped only when all four have converged; a
+// converged column inside an active group is recomputed harmlessly (its
+// alpha and beta are 0, its dot products unused).
 #include <algorithm>
+#include <type_traits>
 
 #include "mc_internal.cuh"
 
@@ -15,8 +20,7 @@ namespace mc {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kCols = 128;
+constexpr int kRowLanes = 8;
 
 struct Dot2 {   // compensated FP32 dot product (TwoProduct + TwoSum)
   float s = 0.f, c = 0.f;
@@ -35,10 +39,21 @@ struct Dot2 {   // compensated FP32 dot product (TwoProduct + TwoSum)
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
-// combine the 8 row lanes' partial sums of this CTA's 128 columns, fixed order
-__device__ __forceinline__ void cta_partials4(const double v[4], double (*sh)[kCols + 1],
+// the thread's column lane and row lane
+template <int LANES>
+__device__ __forceinline__ int col_lane() { return threadIdx.x % LANES; }
+template <int LANES>
+__device__ __forceinline__ int row_lane() { return threadIdx.x / LANES; }
+template <int LANES>
+__device__ __forceinline__ int first_col() {
+  return blockIdx.x * (4 * LANES) + col_lane<LANES>() * 4;
+}
+
+// combine the 8 row lanes' partial sums of this CTA's 4 * LANES columns, fixed order
+template <int LANES>
+__device__ __forceinline__ void cta_partials4(const double v[4], double (*sh)[4 * LANES + 1],
                                               double* out, int W, int col0, bool valid) {
-  const int lane = threadIdx.x & 31, rl = threadIdx.x >> 5;
+  const int lane = col_lane<LANES>(), rl = row_lane<LANES>();
 #pragma unroll
   for (int c = 0; c < 4; ++c) sh[rl][lane * 4 + c] = v[c];
   __syncthreads();
@@ -47,7 +62,7 @@ __device__ __forceinline__ void cta_partials4(const double v[4], double (*sh)[kC
     for (int c = 0; c < 4; ++c) {
       double s = sh[0][lane * 4 + c];
 #pragma unroll
-      for (int r = 1; r < 8; ++r) s += sh[r][lane * 4 + c];
+      for (int r = 1; r < kRowLanes; ++r) s += sh[r][lane * 4 + c];
       out[(long long)blockIdx.y * W + col0 + c] = s;
     }
   }
@@ -58,20 +73,22 @@ __device__ __forceinline__ bool group_done(const int32_t* done, int col0) {
   return done[col0] && done[col0 + 1] && done[col0 + 2] && done[col0 + 3];
 }
 
-__global__ void __launch_bounds__(kThreads) k4_init(CgGeom g, const double* __restrict__ B,
-                                                    float* __restrict__ X, float* __restrict__ R,
-                                                    float* __restrict__ P,
-                                                    const float* __restrict__ inv_diag,
-                                                    double* __restrict__ partials) {
-  __shared__ double sh[8][kCols + 1];
-  const int col0 = blockIdx.x * kCols + (threadIdx.x & 31) * 4;
-  const int rl = threadIdx.x >> 5;
+template <int LANES>
+__global__ void __launch_bounds__(LANES * kRowLanes) k4_init(CgGeom g, const double* __restrict__ B,
+                                                             float* __restrict__ X,
+                                                             float* __restrict__ R,
+                                                             float* __restrict__ P,
+                                                             const float* __restrict__ inv_diag,
+                                                             double* __restrict__ partials) {
+  __shared__ double sh[kRowLanes][4 * LANES + 1];
+  const int col0 = first_col<LANES>();
+  const int rl = row_lane<LANES>();
   const bool valid = col0 < g.W;
   const long long r0 = (long long)blockIdx.y * g.rows_per_block;
   const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
   Dot2 rz[4], bb[4];
   if (valid) {
-    for (long long i = r0 + rl; i < r1; i += 8) {
+    for (long long i = r0 + rl; i < r1; i += kRowLanes) {
       const long long e = i * g.W + col0;
       const float d = inv_diag[i];
       float b[4], z[4];
@@ -91,10 +108,10 @@ __global__ void __launch_bounds__(kThreads) k4_init(CgGeom g, const double* __re
   double v[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) v[c] = rz[c].value();
-  cta_partials4(v, sh, partials, g.W, col0, valid);
+  cta_partials4<LANES>(v, sh, partials, g.W, col0, valid);
 #pragma unroll
   for (int c = 0; c < 4; ++c) v[c] = bb[c].value();
-  cta_partials4(v, sh, partials + plane, g.W, col0, valid);
+  cta_partials4<LANES>(v, sh, partials + plane, g.W, col0, valid);
 }
 
 // sum of the neighbours' float4 rows, ascending, loaded four rows at a time
@@ -180,21 +197,23 @@ __device__ __forceinline__ CsrSlice stage_csr(const CgGeom& g, const int32_t* __
   return CsrSlice{row_ptr + r0, col_idx};
 }
 
-__global__ void __launch_bounds__(kThreads) k4_L(CgGeom g, const int32_t* __restrict__ row_ptr,
-                                                 const int32_t* __restrict__ col_idx,
-                                                 const int32_t* __restrict__ deg,
-                                                 const float* __restrict__ inv_d, int kind,
-                                                 const float* __restrict__ P,
-                                                 float* __restrict__ T,
-                                                 const int32_t* __restrict__ done) {
+template <int LANES>
+__global__ void __launch_bounds__(LANES * kRowLanes) k4_L(CgGeom g,
+                                                          const int32_t* __restrict__ row_ptr,
+                                                          const int32_t* __restrict__ col_idx,
+                                                          const int32_t* __restrict__ deg,
+                                                          const float* __restrict__ inv_d,
+                                                          int kind, const float* __restrict__ P,
+                                                          float* __restrict__ T,
+                                                          const int32_t* __restrict__ done) {
   extern __shared__ int32_t smem_csr[];
-  const int col0 = blockIdx.x * kCols + (threadIdx.x & 31) * 4;
-  const int rl = threadIdx.x >> 5;
+  const int col0 = first_col<LANES>();
+  const int rl = row_lane<LANES>();
   const long long r0 = (long long)blockIdx.y * g.rows_per_block;
   const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
   const CsrSlice cs = stage_csr(g, row_ptr, col_idx, r0, r1, smem_csr);
   if (col0 >= g.W || group_done(done, col0)) return;
-  for (long long i = r0 + rl; i < r1; i += 8) {
+  for (long long i = r0 + rl; i < r1; i += kRowLanes) {
     const float4 s = gather4(P, cs.ci, cs.rp[i - r0], cs.rp[i - r0 + 1], g.W, col0);
     const float4 p = ld4(P + i * g.W + col0);
     float4 t;
@@ -210,28 +229,31 @@ __global__ void __launch_bounds__(kThreads) k4_L(CgGeom g, const int32_t* __rest
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k4_LT(CgGeom g, const int32_t* __restrict__ row_ptr,
-                                                  const int32_t* __restrict__ col_idx,
-                                                  const int32_t* __restrict__ deg,
-                                                  const float* __restrict__ inv_d, int kind,
-                                                  const uint8_t* __restrict__ is_anchor,
-                                                  const float* __restrict__ T,
-                                                  const float* __restrict__ P,
-                                                  float* __restrict__ Q,
-                                                  const int32_t* __restrict__ done,
-                                                  double* __restrict__ partials) {
+template <int LANES>
+__global__ void __launch_bounds__(LANES * kRowLanes) k4_LT(CgGeom g,
+                                                           const int32_t* __restrict__ row_ptr,
+                                                           const int32_t* __restrict__ col_idx,
+                                                           const int32_t* __restrict__ deg,
+                                                           const float* __restrict__ inv_d,
+                                                           int kind,
+                                                           const uint8_t* __restrict__ is_anchor,
+                                                           const float* __restrict__ T,
+                                                           const float* __restrict__ P,
+                                                           float* __restrict__ Q,
+                                                           const int32_t* __restrict__ done,
+                                                           double* __restrict__ partials) {
   // (the CSR slice stays in global memory here: staging it costs this kernel
   // four registers and an occupancy step, more than the shorter load chain
   // saves; measured on the 99,856-vertex grid)
-  __shared__ double sh[8][kCols + 1];
-  const int col0 = blockIdx.x * kCols + (threadIdx.x & 31) * 4;
-  const int rl = threadIdx.x >> 5;
+  __shared__ double sh[kRowLanes][4 * LANES + 1];
+  const int col0 = first_col<LANES>();
+  const int rl = row_lane<LANES>();
   const bool valid = col0 < g.W && !group_done(done, col0);
   const long long r0 = (long long)blockIdx.y * g.rows_per_block;
   const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
   Dot2 pap[4];
   if (valid) {
-    for (long long j = r0 + rl; j < r1; j += 8) {
+    for (long long j = r0 + rl; j < r1; j += kRowLanes) {
       const int b = row_ptr[j], e = row_ptr[j + 1];
       const float4 a = kind == 0 ? wgather4(T, inv_d, col_idx, b, e, g.W, col0)
                                  : gather4(T, col_idx, b, e, g.W, col0);
@@ -258,20 +280,21 @@ __global__ void __launch_bounds__(kThreads) k4_LT(CgGeom g, const int32_t* __res
   double v[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) v[c] = pap[c].value();
-  cta_partials4(v, sh, partials, g.W, col0, col0 < g.W);
+  cta_partials4<LANES>(v, sh, partials, g.W, col0, col0 < g.W);
 }
 
-__global__ void __launch_bounds__(kThreads) k4_update(CgGeom g, float* __restrict__ X,
-                                                      float* __restrict__ R,
-                                                      const float* __restrict__ P,
-                                                      const float* __restrict__ Q,
-                                                      const float* __restrict__ inv_diag,
-                                                      const double* __restrict__ alpha,
-                                                      const int32_t* __restrict__ done,
-                                                      double* __restrict__ partials) {
-  __shared__ double sh[8][kCols + 1];
-  const int col0 = blockIdx.x * kCols + (threadIdx.x & 31) * 4;
-  const int rl = threadIdx.x >> 5;
+template <int LANES>
+__global__ void __launch_bounds__(LANES * kRowLanes) k4_update(CgGeom g, float* __restrict__ X,
+                                                               float* __restrict__ R,
+                                                               const float* __restrict__ P,
+                                                               const float* __restrict__ Q,
+                                                               const float* __restrict__ inv_diag,
+                                                               const double* __restrict__ alpha,
+                                                               const int32_t* __restrict__ done,
+                                                               double* __restrict__ partials) {
+  __shared__ double sh[kRowLanes][4 * LANES + 1];
+  const int col0 = first_col<LANES>();
+  const int rl = row_lane<LANES>();
   const bool valid = col0 < g.W && !group_done(done, col0);
   const long long r0 = (long long)blockIdx.y * g.rows_per_block;
   const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
@@ -279,7 +302,7 @@ __global__ void __launch_bounds__(kThreads) k4_update(CgGeom g, float* __restric
   if (valid) {
     const float a0 = (float)alpha[col0], a1 = (float)alpha[col0 + 1];
     const float a2 = (float)alpha[col0 + 2], a3 = (float)alpha[col0 + 3];
-    for (long long i = r0 + rl; i < r1; i += 8) {
+    for (long long i = r0 + rl; i < r1; i += kRowLanes) {
       const long long e = i * g.W + col0;
       const float4 x = ld4(X + e), r = ld4(R + e), p = ld4(P + e), q = ld4(Q + e);
       const float d = inv_diag[i];
@@ -298,25 +321,26 @@ __global__ void __launch_bounds__(kThreads) k4_update(CgGeom g, float* __restric
   double v[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) v[c] = rz[c].value();
-  cta_partials4(v, sh, partials, g.W, col0, col0 < g.W);
+  cta_partials4<LANES>(v, sh, partials, g.W, col0, col0 < g.W);
 #pragma unroll
   for (int c = 0; c < 4; ++c) v[c] = rr[c].value();
-  cta_partials4(v, sh, partials + plane, g.W, col0, col0 < g.W);
+  cta_partials4<LANES>(v, sh, partials + plane, g.W, col0, col0 < g.W);
 }
 
-__global__ void __launch_bounds__(kThreads) k4_dir(CgGeom g, const float* __restrict__ R,
-                                                   float* __restrict__ P,
-                                                   const float* __restrict__ inv_diag,
-                                                   const double* __restrict__ beta,
-                                                   const int32_t* __restrict__ done) {
-  const int col0 = blockIdx.x * kCols + (threadIdx.x & 31) * 4;
-  const int rl = threadIdx.x >> 5;
+template <int LANES>
+__global__ void __launch_bounds__(LANES * kRowLanes) k4_dir(CgGeom g, const float* __restrict__ R,
+                                                            float* __restrict__ P,
+                                                            const float* __restrict__ inv_diag,
+                                                            const double* __restrict__ beta,
+                                                            const int32_t* __restrict__ done) {
+  const int col0 = first_col<LANES>();
+  const int rl = row_lane<LANES>();
   if (col0 >= g.W || group_done(done, col0)) return;
   const float b0 = (float)beta[col0], b1 = (float)beta[col0 + 1];
   const float b2 = (float)beta[col0 + 2], b3 = (float)beta[col0 + 3];
   const long long r0 = (long long)blockIdx.y * g.rows_per_block;
   const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
-  for (long long i = r0 + rl; i < r1; i += 8) {
+  for (long long i = r0 + rl; i < r1; i += kRowLanes) {
     const long long e = i * g.W + col0;
     const float4 r = ld4(R + e), p = ld4(P + e);
     const float d = inv_diag[i];
@@ -327,36 +351,75 @@ __global__ void __launch_bounds__(kThreads) k4_dir(CgGeom g, const float* __rest
 
 }  // namespace
 
+// column lanes per CTA for W columns: the fewest idle columns, the widest tile on ties
+static int cg4_lanes(int W) {
+  int best = 32;
+  long long best_idle = -1;
+  for (int lanes : {32, 16, 8}) {
+    const long long cols = 4LL * lanes;
+    const long long idle = (W + cols - 1) / cols * cols - W;
+    if (best_idle < 0 || idle < best_idle) {
+      best = lanes;
+      best_idle = idle;
+    }
+  }
+  return best;
+}
+
+template <typename Fn>
+static void with_lanes(int W, Fn&& fn) {
+  switch (cg4_lanes(W)) {
+    case 32: fn(std::integral_constant<int, 32>()); break;
+    case 16: fn(std::integral_constant<int, 16>()); break;
+    default: fn(std::integral_constant<int, 8>()); break;
+  }
+}
+
+template <int LANES>
+static dim3 grid4(const CgGeom& g) {
+  return dim3((g.W + 4 * LANES - 1) / (4 * LANES), g.row_blocks);
+}
+
 bool cg4_applies(int W, int single) { return single && (W % 4) == 0; }
 
 void cg4_init(const CgGeom& g, const double* B, float* X, float* R, float* P,
               const float* inv_diag, double* partials, cudaStream_t s) {
-  dim3 grid((g.W + kCols - 1) / kCols, g.row_blocks);
-  k4_init<<<grid, kThreads, 0, s>>>(g, B, X, R, P, inv_diag, partials);
+  with_lanes(g.W, [&](auto lanes) {
+    constexpr int LN = decltype(lanes)::value;
+    k4_init<LN><<<grid4<LN>(g), LN * kRowLanes, 0, s>>>(g, B, X, R, P, inv_diag, partials);
+  });
 }
 
 void cg4_op(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* deg,
             const float* inv_d, int kind, const uint8_t* is_anchor, const float* P, float* T,
             float* Q, const int32_t* done, double* partials, cudaStream_t s, cudaEvent_t* ev) {
-  dim3 grid((g.W + kCols - 1) / kCols, g.row_blocks);
   const size_t smem = g.csr_cap > 0 ? sizeof(int32_t) * (g.rows_per_block + 1 + g.csr_cap) : 0;
-  k4_L<<<grid, kThreads, smem, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, P, T, done);
-  if (ev) cudaEventRecord(ev[1], s);
-  k4_LT<<<grid, kThreads, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind, is_anchor, T, P, Q,
-                                  done, partials);
+  with_lanes(g.W, [&](auto lanes) {
+    constexpr int LN = decltype(lanes)::value;
+    k4_L<LN><<<grid4<LN>(g), LN * kRowLanes, smem, s>>>(g, row_ptr, col_idx, deg, inv_d, kind,
+                                                        P, T, done);
+    if (ev) cudaEventRecord(ev[1], s);
+    k4_LT<LN><<<grid4<LN>(g), LN * kRowLanes, 0, s>>>(g, row_ptr, col_idx, deg, inv_d, kind,
+                                                      is_anchor, T, P, Q, done, partials);
+  });
 }
 
 void cg4_update(const CgGeom& g, float* X, float* R, const float* P, const float* Q,
                 const float* inv_diag, const double* alpha, const int32_t* done,
                 double* partials, cudaStream_t s) {
-  dim3 grid((g.W + kCols - 1) / kCols, g.row_blocks);
-  k4_update<<<grid, kThreads, 0, s>>>(g, X, R, P, Q, inv_diag, alpha, done, partials);
+  with_lanes(g.W, [&](auto lanes) {
+    constexpr int LN = decltype(lanes)::value;
+    k4_update<LN><<<grid4<LN>(g), LN * kRowLanes, 0, s>>>(g, X, R, P, Q, inv_diag, alpha, done,
+                                                          partials);
+  });
 }
 
 void cg4_dir(const CgGeom& g, const float* R, float* P, const float* inv_diag, const double* beta,
              const int32_t* done, cudaStream_t s) {
-  dim3 grid((g.W + kCols - 1) / kCols, g.row_blocks);
-  k4_dir<<<grid, kThreads, 0, s>>>(g, R, P, inv_diag, beta, done);
+  with_lanes(g.W, [&](auto lanes) {
+    constexpr int LN = decltype(lanes)::value;
+    k4_dir<LN><<<grid4<LN>(g), LN * kRowLanes, 0, s>>>(g, R, P, inv_diag, beta, done);
+  });
 }
 
 }  // namespace mc
