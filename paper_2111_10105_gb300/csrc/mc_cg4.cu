@@ -283,8 +283,11 @@ __global__ void __launch_bounds__(LANES * kRowLanes) k4_LT(CgGeom g,
   cta_partials4<LANES>(v, sh, partials, g.W, col0, col0 < g.W);
 }
 
+// (at most 64 registers: 1,024 resident threads per SM, each with two rows of
+// loads in flight)
 template <int LANES>
-__global__ void __launch_bounds__(LANES * kRowLanes) k4_update(CgGeom g, float* __restrict__ X,
+__global__ void __launch_bounds__(LANES * kRowLanes, 1024 / (LANES * kRowLanes))
+    k4_update(CgGeom g, float* __restrict__ X,
                                                                float* __restrict__ R,
                                                                const float* __restrict__ P,
                                                                const float* __restrict__ Q,
@@ -302,10 +305,7 @@ __global__ void __launch_bounds__(LANES * kRowLanes) k4_update(CgGeom g, float* 
   if (valid) {
     const float a0 = (float)alpha[col0], a1 = (float)alpha[col0 + 1];
     const float a2 = (float)alpha[col0 + 2], a3 = (float)alpha[col0 + 3];
-    for (long long i = r0 + rl; i < r1; i += kRowLanes) {
-      const long long e = i * g.W + col0;
-      const float4 x = ld4(X + e), r = ld4(R + e), p = ld4(P + e), q = ld4(Q + e);
-      const float d = inv_diag[i];
+    auto step = [&](long long e, float4 x, float4 r, float4 p, float4 q, float d) {
       st4(X + e, make_float4(fmaf(a0, p.x, x.x), fmaf(a1, p.y, x.y), fmaf(a2, p.z, x.z),
                              fmaf(a3, p.w, x.w)));
       const float4 rn = make_float4(fmaf(-a0, q.x, r.x), fmaf(-a1, q.y, r.y), fmaf(-a2, q.z, r.z),
@@ -315,6 +315,22 @@ __global__ void __launch_bounds__(LANES * kRowLanes) k4_update(CgGeom g, float* 
       rz[1].add(rn.y, rn.y * d); rr[1].add(rn.y, rn.y);
       rz[2].add(rn.z, rn.z * d); rr[2].add(rn.z, rn.z);
       rz[3].add(rn.w, rn.w * d); rr[3].add(rn.w, rn.w);
+    };
+    // two rows' loads in flight before either row's stores (rows in ascending order)
+    const long long stride = (long long)kRowLanes * g.W;
+    long long i = r0 + rl;
+    for (; i + kRowLanes < r1; i += 2 * kRowLanes) {
+      const long long e = i * g.W + col0;
+      const float4 x0 = ld4(X + e), rv0 = ld4(R + e), p0 = ld4(P + e), q0 = ld4(Q + e);
+      const float4 x1 = ld4(X + e + stride), rv1 = ld4(R + e + stride);
+      const float4 p1 = ld4(P + e + stride), q1 = ld4(Q + e + stride);
+      const float d0 = inv_diag[i], d1 = inv_diag[i + kRowLanes];
+      step(e, x0, rv0, p0, q0, d0);
+      step(e + stride, x1, rv1, p1, q1, d1);
+    }
+    if (i < r1) {
+      const long long e = i * g.W + col0;
+      step(e, ld4(X + e), ld4(R + e), ld4(P + e), ld4(Q + e), inv_diag[i]);
     }
   }
   const long long plane = (long long)g.row_blocks * g.W;
