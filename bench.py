@@ -9,9 +9,12 @@ workload is the 20 000-vertex torus sequence (F = 256 frames, k = 32,
 12-bit coefficients, 16-bit dictionary and anchors, 50 anchors) in the FP64
 mode; `--workload grid316_F512_k64 --precision tf32` measures the
 mixed-precision form on the 99 856-vertex grid sequence, `--workload
-batched64 --precision tf32` 64 ragged sequences per step, and `--workload
+batched64 --precision tf32` 64 ragged sequences per step, `--workload
 learned` the 262 144-vertex grid coded segment by segment with the learned
-warm starts against the plain ones.
+warm starts against the plain ones, `--workload blocks` the torus coded as
+8 blocks of 32 frames, `--workload rd` the rate-distortion sweep over k and
+coefficient bits, and `--workload anchors` the anchor-selection study
+(random against farthest-point anchors).
 
 Prints ONE JSON line (rank 0).  Under torchrun each rank runs an independent
 replica on its own GPU (the codec does not shard a sequence); `value` is the
@@ -711,6 +714,98 @@ def run_rd(args):
     return 0
 
 
+def run_anchors(args):
+    """Anchor-selection study on the torus sequence (20,000 vertices, 256
+    frames, k 32, 12 bits, FP64, factored solve): n_c in {25, 50, 100, 200}
+    anchors chosen at random (three seeded draws, the codec's own rule) or
+    spread evenly by farthest points over the first frame
+    (mesh_codec_farthest_anchors); NMSE, CG iterations and encode + decode
+    throughput per point (Section III-B asks for uniformly distributed
+    anchors; Section V leaves the best choice open).  `value` is the
+    throughput of the farthest-point set at the workload's own 50 anchors."""
+    import torch
+
+    from oracle import metrics
+    from paper_2111_10105_gb300 import MeshCodec, codec as cb
+    from synth import make_sequence, config_spec
+
+    world, rank, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = config_spec(DEFAULT_WORKLOAD)
+    tris, pos = make_sequence(spec)
+    F, n = pos.shape[0], pos.shape[1]
+    pos_d = torch.from_numpy(pos).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    points, value, launches = [], None, 0
+    sampler = ClockSampler()
+    sampler.start()
+    for n_c in (25, 50, 100, 200):
+        sets = []
+        for draw in range(3):
+            g = torch.Generator(device="cpu").manual_seed(7919 * n_c + draw)
+            sets.append((f"random{draw}", torch.randperm(n, generator=g)[:n_c].sort().values))
+        sets.append(("farthest", cb.farthest_anchors(pos_d[0].contiguous(), n_c, 0)))
+        for rule, anchors in sets:
+            kw = dict(n_frames=F, rank=spec.rank, n_anchors=n_c, seed=spec.seed,
+                      coeff_bits=spec.coeff_bits, dict_bits=spec.dict_bits,
+                      anchor_bits=spec.anchor_bits, oi_sweeps=SWEEPS, solve_mode=1)
+            with MeshCodec(tris, n, anchors=anchors, **kw) as mc:
+                out = torch.empty(mc.stream_bytes, dtype=torch.uint8, device=dev)
+                rec = torch.empty_like(pos_d)
+                for _ in range(max(args.warmup, 1)):
+                    mc.encode(pos_d, out=out, stream=stream)
+                    mc.decode(out, out=rec, stream=stream)
+                ms = 0.0
+                for _ in range(args.steps):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    mc.encode(pos_d, out=out, stream=stream)
+                    mc.decode(out, out=rec, stream=stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms += e0.elapsed_time(e1)
+                st = mc.stats()
+                launches += st["launches_encode"] + st["launches_decode"]
+                r = cb.rates(1, n_vertices=n, n_triangles=tris.shape[0], **kw)
+                vfs = n * F * args.steps / (ms / 1e3)
+                points.append({"n_anchors": n_c, "rule": rule, "q_a": r["q_a"],
+                               "stream_bpvf": r["stream"],
+                               "nmse": metrics.nmse(pos, rec.cpu().numpy()),
+                               "cg_iters_mean": st["cg_iters_mean"],
+                               "cg_iters_max": st["cg_iters_max"],
+                               "vertex_frames_per_s": vfs})
+                if n_c == spec.n_anchors and rule == "farthest":
+                    value = vfs
+    clocks = sampler.stop()
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": n * F / value * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "anchors", "mesh": spec.mesh, "n": n, "F": F,
+                       "k": spec.rank, "n_anchors": [25, 50, 100, 200],
+                       "rules": ["random (3 seeded draws)", "farthest points from vertex 0, frame 0"],
+                       "l2": "flushed (256 MiB write) before every step",
+                       "parallelism": f"replicas x{world}"},
+            "points": points, "clocks": clocks, "gpu_launches": launches, "roofline": None,
+            "cpu_baseline": None, "e2e": None,
+        }
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def run_learned(args):
     """The 512x512 grid (262,144 vertices, F = 300 per segment, k = 64, 2,621
     anchors) as one coherent sequence coded segment by segment.  Each timed
@@ -915,6 +1010,8 @@ def main(argv=None):
         return run_blocks(args)
     if args.workload == "rd":
         return run_rd(args)
+    if args.workload == "anchors":
+        return run_anchors(args)
     return run_ours(args)
 
 

@@ -158,6 +158,22 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_create(const mesh_codec_params_t* 
                                       const int32_t* anchors, int anchors_on_device,
                                       void* stream, mesh_codec_t** out);
 
+/* Anchors spread evenly over a pose (Section III-B asks for n_c uniformly
+ * distributed anchor vertices; mesh_codec_create draws them at random when
+ * given none): greedy farthest-point selection in Euclidean distance.  From
+ * vertex `start`, n_c - 1 times the vertex farthest from its nearest chosen
+ * vertex joins the set (squared distances formed as (dx*dx + dy*dy) + dz*dz,
+ * every operation rounded separately; equal distances: the lower index).
+ *   xyz:     device float64 [n][3], e.g. the first frame of the sequence.
+ *   anchors: device int32 [n_c], written in ascending order, ready for
+ *            mesh_codec_create.
+ * Needs 1 <= n_c <= n and 0 <= start < n.  Allocates its scratch (8n + 4n_c
+ * bytes and about 10 KB) on `stream` and frees it there; one kernel launch
+ * per anchor.  Errors: MC_E_INVALID_ARG, MC_E_OOM, MC_E_CUDA. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_farthest_anchors(int n, int n_c, const double* xyz,
+                                                               int start, int32_t* anchors,
+                                                               void* stream);
+
 /* Exact size in bytes of every bitstream this handle produces. */
 MESH_CODEC_API mesh_codec_status_t mesh_codec_encoded_size(const mesh_codec_t* h, size_t* bytes);
 

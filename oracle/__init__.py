@@ -26,6 +26,9 @@ steps in order:
 * ``blocks``   - the blocks variant (Section III-A, Algorithm 1 across
                  blocks) with the difference coding of consecutive
                  dictionaries (Section IV, Fig. 6).
+* ``anchors``  - evenly spread anchors by greedy farthest points, the
+                 alternative to the random choice in the anchor-selection
+                 study (Section III-B, Section V).
 * ``mlp``, ``warm`` - the learned warm start (not in the paper): the
                  perceptron in FP64 and its input features.
 

@@ -115,12 +115,15 @@ def _encode_section(values, lo, hi, bits):
     return w + b"\0" * (_pad8(len(w)) - len(w))
 
 
-def encode(tris, positions, p, return_info=False, basis=None, dict_ref=None, dict_bits=None):
+def encode(tris, positions, p, return_info=False, basis=None, dict_ref=None, dict_bits=None,
+           anchors=None):
     """Encodes one block.  `basis` (three F x k matrices) replaces the
     orthogonal iterations from the seeded start (the blocks variant, Section
     III-A, supplies its own U[i]); with `dict_ref` (three F x k matrices) the
     dictionary section carries U - dict_ref (the difference coding of
-    consecutive dictionaries, Section IV, Fig. 6) in `dict_bits` bits."""
+    consecutive dictionaries, Section IV, Fig. 6) in `dict_bits` bits.
+    `anchors` (p.n_anchors strictly increasing vertex indices) replaces the
+    seeded anchor choice."""
     positions = np.asarray(positions, dtype=np.float64)
     F, n, three = positions.shape
     assert three == 3 and F == p.n_frames
@@ -129,7 +132,13 @@ def encode(tris, positions, p, return_info=False, basis=None, dict_ref=None, dic
         raise ValueError("rank must satisfy 1 <= k <= F")
     db = p.dict_bits if dict_bits is None else dict_bits
     row_ptr, col_idx, deg = graph.build_adjacency(tris, n)
-    anchors = select_anchors(n, p.n_anchors, p.seed)
+    if anchors is None:
+        anchors = select_anchors(n, p.n_anchors, p.seed)
+    else:
+        anchors = np.asarray(anchors, dtype=np.int32)
+        if anchors.shape != (p.n_anchors,) or (anchors.size and (
+                anchors[0] < 0 or anchors[-1] >= n or np.any(np.diff(anchors) <= 0))):
+            raise ValueError("anchors must be n_anchors strictly increasing indices in [0, n)")
 
     header = bytearray(HEADER_BYTES)
     total = stream_size(n, F, k, p.n_anchors, p.coeff_bits, db, p.anchor_bits)

@@ -115,6 +115,8 @@ _SIGS = {
     "mesh_codec_mlp_fit_normalizer": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P]),
     "mesh_codec_mlp_get_normalizer": (ctypes.c_int, [_P, _P, _P, _P]),
     "mesh_codec_mlp_destroy": (None, [_P]),
+    "mesh_codec_farthest_anchors": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.c_int,
+                                                   _P, _P]),
     "mesh_codec_nearest_anchor": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, _P, _P,
                                                  _P]),
     "mesh_codec_warm_features": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P,
@@ -217,7 +219,10 @@ class MeshCodec:
         anc_ptr = None
         self._anc_t = None
         if anchors is not None:
-            self._anc_t = torch.as_tensor(np.asarray(anchors, dtype=np.int32)).cuda()
+            if isinstance(anchors, torch.Tensor):
+                self._anc_t = anchors.to(device="cuda", dtype=torch.int32).contiguous()
+            else:
+                self._anc_t = torch.as_tensor(np.asarray(anchors, dtype=np.int32)).cuda()
             anc_ptr = ctypes.c_void_p(self._anc_t.data_ptr())
         h = ctypes.c_void_p()
         st = lib.mesh_codec_create(ctypes.byref(p), ctypes.c_void_p(tri_t.data_ptr()), 1, anc_ptr,
@@ -592,6 +597,19 @@ class Mlp:
 
 WARM_ANCHORS = 3
 WARM_FEATURES = 16
+
+
+def farthest_anchors(xyz, n_anchors, start=0, stream=None):
+    """n_anchors vertices spread over the pose xyz (CUDA float64 [n, 3]) by
+    greedy farthest-point selection from vertex `start`: CUDA int32
+    [n_anchors], ascending (mesh_codec_farthest_anchors)."""
+    torch = _torch()
+    n = xyz.shape[0]
+    out = torch.empty(int(n_anchors), dtype=torch.int32, device=xyz.device)
+    _check(load_library().mesh_codec_farthest_anchors(
+        n, int(n_anchors), _dptr(xyz, torch.float64, (n, 3)), int(start), _dptr(out),
+        _stream_ptr(stream)), "mesh_codec_farthest_anchors")
+    return out
 
 
 def nearest_anchors(rest, anchors, stream=None):
