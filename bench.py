@@ -56,14 +56,25 @@ LEARNED_OI_CAP = 100
 LEARNED_FIELDS = 16          # learned workload motion: 16 fields,
 LEARNED_CYCLES = 8           # [0.5, 3] x 8 cycles per 300-frame segment
 LEARNED_CG_RTOL = 1e-8
-# DRAM bytes (read + write) per launch from ncu captures of exactly these
-# configurations (workload, precision, refine, CG columns, kernel), with the
-# profiles/ summary they come from; a kernel changed since is to be removed
+# DRAM bytes (read + write) per launch with every column active, from ncu
+# captures of exactly these configurations (workload, precision, refine, CG
+# columns, kernel), with the profiles/ summary they come from; a kernel
+# changed since is to be removed.  The bench scales them by the mean fraction
+# of active columns, as it does the algorithmic bytes.  Which vertices are
+# anchors does not change a launch's data flow (same adjacency and columns).
 MEASURED_TRAFFIC = {
     ("torus200x100_F256_k32", "fp64", 0, 96, "k_cg_LT"):
         (31.56e6, "profiles/k_cg_L_LT_torus200x100_F256_k32_fp64.md"),
     ("torus200x100_F256_k32", "fp64", 0, 96, "k_cg_L"):
         (16.11e6, "profiles/k_cg_L_LT_torus200x100_F256_k32_fp64.md"),
+    ("grid316_F512_k64", "tf32", 0, 192, "k_cg_update"):
+        (422.43e6, "profiles/k4_grid316_F512_k64_tf32.md"),
+    ("grid316_F512_k64", "tf32", 0, 192, "k_cg_LT"):
+        (212.66e6, "profiles/k4_grid316_F512_k64_tf32.md"),
+    ("grid316_F512_k64", "tf32", 0, 192, "k_cg_L"):
+        (120.34e6, "profiles/k4_grid316_F512_k64_tf32.md"),
+    ("grid316_F512_k64", "tf32", 0, 192, "k_cg_dir"):
+        (183.06e6, "profiles/k4_grid316_F512_k64_tf32.md"),
 }
 
 
@@ -226,39 +237,43 @@ def roofline(profile, stats, n, W, nnz, n_c, peaks, single):
 
 
 # ---------------------------------------------------------------- oracle legs
-def oracle_sample(workload, frames, repeats=1):
+def oracle_sample(workload, frames, repeats=1, anchor_rule="random"):
     """Time the FP64 oracle (single-threaded BLAS) on the first `frames`
-    frames of the workload's sequence, in a child process."""
+    frames of the workload's sequence, in a child process, with the same
+    anchor rule as the GPU run (the farthest-point selection over frame 0 is
+    set up before the timed passes, as the GPU codec's is)."""
     env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1",
                MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
     code = (
         "import sys, time, json; sys.path.insert(0, %r)\n"
         "from synth import make_sequence, config_spec\n"
-        "from oracle import codec, metrics\n"
+        "from oracle import anchors, codec, metrics\n"
         "spec = config_spec(%r); tris, pos = make_sequence(spec); pos = pos[:%d].copy()\n"
         "p = codec.Params(n_frames=pos.shape[0], rank=min(spec.rank, pos.shape[0]),"
         " n_anchors=spec.n_anchors, seed=spec.seed, oi_sweeps=%d)\n"
+        "anc = anchors.farthest_point(pos[0], spec.n_anchors, 0) if %r == 'farthest' else None\n"
         "out = []\n"
         "for _ in range(%d):\n"
-        "    t0 = time.perf_counter(); blob = codec.encode(tris, pos, p)\n"
+        "    t0 = time.perf_counter(); blob = codec.encode(tris, pos, p, anchors=anc)\n"
         "    t1 = time.perf_counter(); rec = codec.decode(blob, tris); t2 = time.perf_counter()\n"
         "    out.append([t1 - t0, t2 - t1])\n"
         "print(json.dumps({'n': pos.shape[1], 'F': pos.shape[0], 'times': out,"
         " 'nmse': metrics.nmse(pos, rec)}))\n"
-    ) % (ROOT, workload, frames, SWEEPS, repeats)
+    ) % (ROOT, workload, frames, SWEEPS, anchor_rule, repeats)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline(workload):
-    res = oracle_sample(workload, CPU_SAMPLE_FRAMES, repeats=1)
+def cpu_baseline(workload, anchor_rule="random"):
+    res = oracle_sample(workload, CPU_SAMPLE_FRAMES, repeats=1, anchor_rule=anchor_rule)
     enc, dec = res["times"][0]
     vf = res["n"] * res["F"]
     return {"value": vf / (enc + dec), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"{workload} first {res['F']} frames (n={res['n']}), one encode+decode, "
-                       f"single-threaded numpy/scipy, encode {enc:.2f} s + decode {dec:.2f} s")}
+            "sample": (f"{workload} first {res['F']} frames (n={res['n']}), {anchor_rule} "
+                       f"anchors, one encode+decode, single-threaded numpy/scipy, "
+                       f"encode {enc:.2f} s + decode {dec:.2f} s")}
 
 
 def run_reference(args):
@@ -266,9 +281,10 @@ def run_reference(args):
     if rank != 0:
         return 0
     for _ in range(args.warmup):
-        oracle_sample(args.workload, REF_SAMPLE_FRAMES, repeats=1)
+        oracle_sample(args.workload, REF_SAMPLE_FRAMES, repeats=1, anchor_rule=args.anchors)
     t0 = time.perf_counter()
-    res = oracle_sample(args.workload, REF_SAMPLE_FRAMES, repeats=args.steps)
+    res = oracle_sample(args.workload, REF_SAMPLE_FRAMES, repeats=args.steps,
+                        anchor_rule=args.anchors)
     wall = time.perf_counter() - t0
     secs = sum(a + b for a, b in res["times"])
     vf = res["n"] * res["F"] * args.steps
@@ -279,7 +295,8 @@ def run_reference(args):
         "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{args.workload} (first {res['F']} frames per step)",
-                   "n": res["n"], "F": res["F"], "sweeps": SWEEPS},
+                   "n": res["n"], "F": res["F"], "sweeps": SWEEPS,
+                   "anchor_rule": args.anchors},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{args.workload} first {res['F']} frames, single-threaded, "
                                    f"{args.steps} encode+decode passes ({wall:.1f} s wall)"},
@@ -296,6 +313,7 @@ def run_ours(args):
 
     from oracle import metrics   # NMSE of the result, computed on the host
     from paper_2111_10105_gb300 import MeshCodec
+    from paper_2111_10105_gb300.codec import farthest_anchors
     from synth import make_sequence, config_spec
 
     world, rank, local = dist_env()
@@ -319,8 +337,11 @@ def run_ours(args):
               anchor_bits=spec.anchor_bits, oi_sweeps=SWEEPS, precision=prec,
               oi_refine_sweeps=1 if prec else 0, cg_rtol=cg_rtol, refine=args.refine,
               solve_mode={"frames": 0, "factored": 1}[args.solve_mode])
-    mc = MeshCodec(tris, n, **kw)
     pos_dev = torch.from_numpy(pos).to(dev)
+    anchors = None
+    if args.anchors == "farthest":   # set up once per connectivity, like the codec itself
+        anchors = farthest_anchors(pos_dev[0].contiguous(), spec.n_anchors, 0)
+    mc = MeshCodec(tris, n, anchors=anchors, **kw)
     bits = torch.empty(mc.stream_bytes, dtype=torch.uint8, device=dev)
     rec = torch.empty_like(pos_dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -367,7 +388,7 @@ def run_ours(args):
     value, seconds = aggregate(vf_local, total_ms / 1e3, world, dist)
 
     # NMSE of this run's reconstruction vs the oracle's stored value
-    ref = nmse_reference(args.workload)
+    ref = nmse_reference(args.workload + (":farthest" if args.anchors == "farthest" else ""))
     nmse = metrics.nmse(pos, rec.cpu().numpy())
     tol = NMSE_RTOL[args.precision]
     nmse_ref = ref[1] if ref and ref[0] == SWEEPS else None
@@ -395,8 +416,9 @@ def run_ours(args):
     measured = MEASURED_TRAFFIC.get((args.workload, args.precision, args.refine, cols,
                                      rl["kernel"]))
     if measured:
-        rl["traffic"] = measured[0]
-        rl["traffic_source"] = measured[1]
+        active = stats["cg_iters_mean"] / max(1, stats["cg_iters_max"])
+        rl["traffic"] = round(measured[0] * active)
+        rl["traffic_source"] = measured[1] + " (x %.4f active columns)" % active
 
     if rank == 0:
         out = {
@@ -411,6 +433,8 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": args.workload, "mesh": spec.mesh, "n": n, "F": F,
                        "k": spec.rank, "anchors": spec.n_anchors,
+                       "anchor_rule": {"farthest": "farthest points over frame 0 from vertex 0",
+                                       "random": "seeded random"}[args.anchors],
                        "bits": [spec.coeff_bits, spec.dict_bits, spec.anchor_bits],
                        "oi_sweeps": SWEEPS, "oi_refine_sweeps": 1 if single else 0,
                        "cg_rtol": cg_rtol, "precision": args.precision, "refine": args.refine,
@@ -429,7 +453,7 @@ def run_ours(args):
             "gpu_launches": launches,
         }
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(args.workload)
+            out["cpu_baseline"] = cpu_baseline(args.workload, args.anchors)
         print(json.dumps(out), flush=True)
     mc.close()
     if dist is not None:
@@ -989,6 +1013,9 @@ def main(argv=None):
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--precision", choices=["fp64", "tf32", "bf16"], default="fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--anchors", choices=["farthest", "random"], default="farthest",
+                    help="anchor rule of the single-sequence workloads: evenly spread "
+                         "(farthest points over the first frame) or the seeded random draw")
     ap.add_argument("--refine", type=int, default=0,
                     help="decoder solve by iterative refinement: FP32 CG corrections to "
                          "10^-r with FP64 residuals (0: off)")
