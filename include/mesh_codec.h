@@ -363,9 +363,11 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_copy_buffer(const mesh_codec_t* h,
 
 /* Kernel timing.  With `every` > 0, each decode records CUDA events on its
  * stream around the kernels of sampled CG iterations and adds their
- * durations to per-kernel totals; 0 turns it off.  Full runs of 32
- * iterations sample their first one (the other 31 replay from a CUDA graph,
- * as without timing); shorter runs sample every `every`-th iteration.
+ * durations to per-kernel totals; 0 turns it off.  A full run of 32
+ * iterations whose first iteration's index is a multiple of `every` samples
+ * its last iteration (the 31 before it replay from a CUDA graph, as without
+ * timing, and the timed launches queue behind them); shorter runs sample
+ * every `every`-th iteration.  Sampling leaves the results unchanged.
  * Either call resets the totals.  mesh_codec_get_profile synchronises the
  * handle's last stream. */
 #define MESH_CODEC_PROF_KERNELS 8
