@@ -220,6 +220,8 @@ void mesh_codec_destroy(mesh_codec_t* h) {
   if (h->ws) cudaFree(h->ws);
   if (h->Gcache) cudaFree(h->Gcache);
   if (h->Gcache_anchors) cudaFree(h->Gcache_anchors);
+  if (h->Glp) cudaFree(h->Glp);
+  if (h->Ahlp) cudaFree(h->Ahlp);
   if (h->stage_pos) cudaFree(h->stage_pos);
   if (h->stage_bits) cudaFree(h->stage_bits);
   if (h->h_status) cudaFreeHost(h->h_status);
@@ -888,15 +890,19 @@ static void decode_finish(mesh_codec* h, double* out, cudaStream_t s, Launches& 
   if (!d.factored) {
     vertex_major_to_frames(Xs, out, F, n, s, L);
   } else {
-    // X_c = Y_c U_c'^T + G A^_c into D [n][3F]
-    dgemm(n, F, k, 3, Strided{Xs, d.Wc, 1, k}, Strided{h->Udeq, 1, k, (long long)F * k},
-          StridedOut{h->D, W, 1, F}, 1, nullptr, s, L);
-    StridedOut acc{h->D, W, 1, F};
-    acc.accumulate = 1;
-    const Strided G = d.cached ? Strided{h->Gcache, h->n_c, 1, 0}
-                               : Strided{Xs + 3 * k, d.Wc, 1, 0};
-    dgemm(n, F, h->n_c, 3, G, Strided{h->Ahat, F, 1, (long long)std::max(h->n_c, 1) * F}, acc, 1,
-          nullptr, s, L);
+    // X_c = Y_c U_c'^T + G A^_c into D [n][3F]: on the tensor cores in the mixed
+    // modes (FP32 solve), in FP64 otherwise (and for the refined solve)
+    const double* Gp = d.cached ? h->Gcache : Xs + 3 * k;
+    const long long g_ld = d.cached ? h->n_c : d.Wc;
+    const bool tc = d.single && !d.refine && h->lp >= 0 && mixed_finish(h, Xs, d.Wc, Gp, g_ld, s, L);
+    if (!tc) {
+      dgemm(n, F, k, 3, Strided{Xs, d.Wc, 1, k}, Strided{h->Udeq, 1, k, (long long)F * k},
+            StridedOut{h->D, W, 1, F}, 1, nullptr, s, L);
+      StridedOut acc{h->D, W, 1, F};
+      acc.accumulate = 1;
+      dgemm(n, F, h->n_c, 3, Strided{Gp, g_ld, 1, 0},
+            Strided{h->Ahat, F, 1, (long long)std::max(h->n_c, 1) * F}, acc, 1, nullptr, s, L);
+    }
     vertex_major_to_frames(h->D, out, F, n, s, L);
     if (d.store) {
       // keep G and its anchors; valid once the decode reports every column converged

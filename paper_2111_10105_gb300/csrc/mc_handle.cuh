@@ -91,6 +91,11 @@ struct mesh_codec {
   size_t tc_part_elems = 0;
   alignas(64) unsigned char map_X[128], map_Qt[128], map_XT[128], map_Wt[128];
   alignas(64) unsigned char map_D[128], map_Ut[128], map_C[128], map_U[128];
+  // decoder's anchor product G A^_c on the tensor cores (own allocation, made
+  // on first use): G [n][ncp] and A^_c^T [3][F][ncp], n_c padded to ncp
+  void *Glp = nullptr, *Ahlp = nullptr;
+  int ncp = 0;
+  alignas(64) unsigned char map_G[128], map_Ah[3][128];
   int refine_sweeps = 0;
   // decoder phases, CG geometry autotuning, own stream for the batch entry points
   DecodeState dec;
@@ -116,4 +121,6 @@ bool mixed_init(mesh_codec* h, cudaStream_t s);
 void mixed_oi_sweeps(mesh_codec* h, int sweeps, cudaStream_t s, Launches& L);
 void mixed_project(mesh_codec* h, cudaStream_t s, Launches& L);
 void mixed_backproject(mesh_codec* h, cudaStream_t s, Launches& L);
+bool mixed_finish(mesh_codec* h, const double* Y, long long y_ld, const double* G, long long g_ld,
+                  cudaStream_t s, Launches& L);
 }  // namespace mc

@@ -131,8 +131,9 @@ bool tc_operand_map(void* map_out, const void* base, int elem_bytes, long long K
 inline int tc_bn(int N) { return N <= 256 ? ((N + 15) / 16) * 16 : 256; }
 size_t tc_smem_bytes(int BN);
 // D = A B^T (FP32 accumulate) on tcgen05; kind 0 tf32, 1 bf16; returns splits used
-// out_kind: 0 fp32, 1 fp32 rounded to tf32, 2 bf16, 3 fp64; element (m, n) of
-// batch b / split z at out[b*sb + z*split_stride + m*s0 + n*s1]
+// out_kind: 0 fp32, 1 fp32 rounded to tf32, 2 bf16, 3 fp64, 4 fp64 added to
+// what out holds (one split only); element (m, n) of batch b / split z at
+// out[b*sb + z*split_stride + m*s0 + n*s1]
 int umma_tn(int kind, const void* mapA, const void* mapB, int M, int N, int K, int batch,
             int splits, void* out, int out_kind, long long s0, long long s1, long long sb,
             long long split_stride, uint32_t* status, cudaStream_t s, Launches& L);

@@ -96,7 +96,7 @@ struct Args {
   int BN, tmem_cols;
   int batch, splits, chunks_per_split, total_chunks;
   void* out;
-  int out_kind;   // 0 fp32, 1 fp32 rounded to tf32, 2 bf16, 3 fp64
+  int out_kind;   // 0 fp32, 1 fp32 rounded to tf32, 2 bf16, 3 fp64, 4 fp64 added to out
   long long s0, s1, sb, split_stride;
   uint32_t* status;
 };
@@ -232,8 +232,10 @@ __global__ void __launch_bounds__(128, 1) k_umma_tn(const __grid_constant__ CUte
               ((float*)a.out)[o] = __uint_as_float(t);
             } else if (a.out_kind == 2) {
               ((__nv_bfloat16*)a.out)[o] = __float2bfloat16_rn(v);
-            } else {
+            } else if (a.out_kind == 3) {
               ((double*)a.out)[o] = (double)v;
+            } else {   // one thread per element (no K split): a plain read-modify-write
+              ((double*)a.out)[o] += (double)v;
             }
           }
         }
