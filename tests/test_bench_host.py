@@ -72,3 +72,18 @@ def test_roofline_arithmetic():
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["achieved"] == pytest.approx(nbytes / 0.3e-3 / 1e9, rel=1e-3)
     assert abs(sum(r["time_share"].values()) - 1.0) < 1e-3
+
+
+def test_stored_oracle_nmse_for_both_anchor_rules():
+    for name in ("torus200x100_F256_k32", "grid316_F512_k64"):
+        for key in (name, name + ":farthest"):
+            sweeps, nmse = bench.nmse_reference(key)
+            assert sweeps == bench.SWEEPS and 0.0 < nmse < 1.0
+    assert bench.nmse_reference("no_such_workload") is None
+
+
+@pytest.mark.parametrize("rule", ["random", "farthest"])
+def test_oracle_leg_runs_with_either_anchor_rule(rule):
+    res = bench.oracle_sample("icosphere4_F64_k16", 4, repeats=1, anchor_rule=rule)
+    assert res["F"] == 4 and res["n"] == 2562 and len(res["times"]) == 1
+    assert 0.0 <= res["nmse"] < 1.0
