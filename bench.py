@@ -399,6 +399,10 @@ def run_ours(args):
     bits_h = torch.empty(mc.stream_bytes, dtype=torch.uint8).pin_memory()
     rec_h = torch.empty((F, n, 3), dtype=torch.float64).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
+    # one untimed step first, as for the device-resident steps: the host-buffer
+    # entry points allocate their staging buffers on first use
+    mc.encode_host(pos_h, out=bits_h, stream=stream)
+    mc.decode_host(bits_h, out=rec_h, stream=stream)
     if dist is not None:
         dist.barrier()
     t0 = time.perf_counter()

@@ -27,7 +27,7 @@ def _seq(seed=31):
     return make_sequence(spec)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_second_decode_solves_only_the_data_columns(precision):
     from paper_2111_10105_gb300 import MeshCodec
     tris, pos = _seq()
@@ -45,7 +45,7 @@ def test_second_decode_solves_only_the_data_columns(precision):
     assert cols_first == pad(3 * 6 + 12)
     assert cols_second == pad(3 * 6)
     e1, e2 = metrics.nmse(pos, first), metrics.nmse(pos, second)
-    assert abs(e1 - e2) <= (1e-9 if precision == 0 else 1e-3) * e1
+    assert abs(e1 - e2) <= {0: 1e-9, 1: 1e-3, 2: 1e-2}[precision] * e1
     if precision == 0:
         o = oc.encode(tris, pos, oc.Params(n_frames=40, rank=6, n_anchors=12, seed=4))
         e_o = metrics.nmse(pos, oc.decode(o, tris))
