@@ -487,6 +487,19 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_mlp_set_params(mesh_codec_mlp_t* m
 MESH_CODEC_API mesh_codec_status_t mesh_codec_mlp_forward(mesh_codec_mlp_t* m, const float* X,
                                                           long long N, float* Y, void* stream);
 
+/* Inference: the network of mesh_codec_mlp_forward with its hidden-to-hidden
+ * product (n_hidden^2 of its multiply-adds per row) on the tcgen05 tensor
+ * cores as a TF32 GEMM: the bfloat16 weights enter exactly, the float32
+ * activations are rounded to TF32 (10-bit mantissa) by the MMA, the products
+ * accumulate in float32.  Outputs agree with mesh_codec_mlp_forward to
+ * about 1e-3 of their scale.  For predictions over many rows (the warm
+ * start's first iterate); training and the gradient checks use the
+ * float32-product forward.  Synchronises `stream` to read the tensor-core
+ * status; when n_hidden is not a multiple of 4 (no TMA description) it runs
+ * mesh_codec_mlp_forward.  Errors: MC_E_INVALID_ARG, MC_E_OOM, MC_E_CUDA. */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_mlp_infer(mesh_codec_mlp_t* m, const float* X,
+                                                        long long N, float* Y, void* stream);
+
 /* Forward pass, loss mean((Y - T)^2) and its gradient for N rows; with
  * update != 0 one Adam step of learning rate lr.  `loss` (host, may be
  * NULL) receives the loss, which synchronises `stream`.

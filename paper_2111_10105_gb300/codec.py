@@ -108,6 +108,7 @@ _SIGS = {
     "mesh_codec_mlp_get_params": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "mesh_codec_mlp_set_params": (ctypes.c_int, [_P, _P, _P]),
     "mesh_codec_mlp_forward": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P, _P]),
+    "mesh_codec_mlp_infer": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P, _P]),
     "mesh_codec_mlp_train_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, ctypes.c_float,
                                                  ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                                  _P]),
@@ -568,6 +569,19 @@ class Mlp:
                                                 N, _dptr(out, torch.float32, (N, self.n_out)),
                                                 _stream_ptr(stream)),
                "mesh_codec_mlp_forward")
+        return out
+
+    def infer(self, X, out=None, stream=None):
+        """forward() with the hidden-to-hidden product on the tensor cores
+        (TF32; mesh_codec_mlp_infer), for predictions over many rows."""
+        torch = _torch()
+        N = X.shape[0]
+        if out is None:
+            out = torch.empty((N, self.n_out), dtype=torch.float32, device=X.device)
+        _check(self._lib.mesh_codec_mlp_infer(self._h, _dptr(X, torch.float32, (N, self.n_in)),
+                                              N, _dptr(out, torch.float32, (N, self.n_out)),
+                                              _stream_ptr(stream)),
+               "mesh_codec_mlp_infer")
         return out
 
     def train_step(self, X, T, lr=1e-3, update=True, want_loss=True, stream=None):

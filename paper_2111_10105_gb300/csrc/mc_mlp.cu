@@ -37,6 +37,13 @@ struct mesh_codec_mlp {
   // input standardisation x' = (x - mu) * inv_sigma (identity until fitted)
   float *mu = nullptr, *inv_sigma = nullptr, *Xn = nullptr;
   double* stat_part = nullptr;
+  // tensor-core inference (mesh_codec_mlp_infer): W2 widened to float32 (exact
+  // from bfloat16, the TF32 operand), the TMA descriptors of H1 and W2, and
+  // the GEMM's status word (made on first use)
+  float* W2f = nullptr;
+  uint32_t *tc_status = nullptr, *tc_status_host = nullptr;
+  alignas(64) unsigned char map_H1[128], map_W2[128];
+  uint64_t tc_launches = 0;
 };
 
 namespace {
@@ -384,6 +391,28 @@ void backward(mesh_codec_mlp* m, const float* X, const float* T, long long N, cu
   else backward_w(m, (const __nv_bfloat16*)m->wbf, X, T, N, s);
 }
 
+// forward_w with the hidden-to-hidden product H1 W2^T (nh x nh of the
+// n_in*nh + nh*nh + nh*n_out multiply-adds per row) on the tensor cores:
+// kind::tf32, the bfloat16 weights exact in TF32, the float32 activations
+// rounded to TF32 by the MMA, float32 accumulation in TMEM.  False when the
+// operands cannot be described for TMA (nothing enqueued then).
+bool infer_tc(mesh_codec_mlp* m, const float* X, long long N, float* Y, cudaStream_t s) {
+  const int nin = m->nin, nh = m->nh, nout = m->nout;
+  const float* p = m->master;
+  const __nv_bfloat16* w = m->wbf;
+  if (!tc_operand_map(m->map_H1, m->H1, 4, nh, N, 1, nh, N * nh, 128)) return false;
+  Launches L{&m->tc_launches};
+  k_standardize<<<grid_for(N * nin), 256, 0, s>>>(X, N, nin, m->mu, m->inv_sigma, m->Xn);
+  sgemm(m, (int)N, nh, nin, (const float*)m->Xn, nin, 1, w + m->oW1, 1, nin, m->H1, nh, 1, s);
+  k_bias_act<<<grid_for(N * nh), 256, 0, s>>>(m->H1, p + m->ob1, N, nh, 1);
+  umma_tn(0, m->map_H1, m->map_W2, (int)N, nh, nh, 1, 1, m->H2, 0, nh, 1, 0, 0, m->tc_status, s,
+          L);
+  k_bias_act<<<grid_for(N * nh), 256, 0, s>>>(m->H2, p + m->ob2, N, nh, 1);
+  sgemm(m, (int)N, nout, nh, m->H2, nh, 1, w + m->oW3, 1, nh, Y, nout, 1, s);
+  k_bias_act<<<grid_for(N * nout), 256, 0, s>>>(Y, p + m->ob3, N, nout, 0);
+  return true;
+}
+
 // ---------------------------------------------------------------- features
 // kWarmFeatures float32 per sample e = f*n + v (frame f of the current
 // segment, vertex v), for the kWarmAnchors nearest anchors a_j = nearest[v][j]:
@@ -602,6 +631,38 @@ mesh_codec_status_t mesh_codec_mlp_forward(mesh_codec_mlp_t* m, const float* X, 
   return cudaGetLastError() == cudaSuccess ? MC_OK : MC_E_CUDA;
 }
 
+mesh_codec_status_t mesh_codec_mlp_infer(mesh_codec_mlp_t* m, const float* X, long long N,
+                                         float* Y, void* stream) {
+  if (!m || !X || !Y || N < 1) return MC_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long chunk = std::min<long long>(N, kForwardChunk);
+  mesh_codec_status_t st = ensure_batch(m, (size_t)chunk);
+  if (st != MC_OK) return st;
+  const int nh = m->nh;
+  if (!m->W2f) {
+    if (cudaMalloc(&m->W2f, sizeof(float) * nh * nh) != cudaSuccess ||
+        cudaMalloc(&m->tc_status, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMallocHost(&m->tc_status_host, sizeof(uint32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return MC_E_OOM;
+    }
+  }
+  if (!tc_operand_map(m->map_W2, m->W2f, 4, nh, nh, 1, nh, (long long)nh * nh, tc_bn(nh)))
+    return mesh_codec_mlp_forward(m, X, N, Y, stream);   // FP32-product forward instead
+  k_from_bf16<<<grid_for((long long)nh * nh), 256, 0, s>>>(m->wbf + m->oW2, m->W2f,
+                                                           (long long)nh * nh);
+  cudaMemsetAsync(m->tc_status, 0, sizeof(uint32_t), s);
+  for (long long r = 0; r < N; r += chunk) {
+    const long long rows = std::min(chunk, N - r);
+    if (!infer_tc(m, X + r * m->nin, rows, Y + r * m->nout, s))
+      forward(m, X + r * m->nin, rows, Y + r * m->nout, s);
+  }
+  cudaMemcpyAsync(m->tc_status_host, m->tc_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MC_E_CUDA;
+  if (*m->tc_status_host != 0) return MC_E_CUDA;
+  return cudaGetLastError() == cudaSuccess ? MC_OK : MC_E_CUDA;
+}
+
 mesh_codec_status_t mesh_codec_mlp_train_step(mesh_codec_mlp_t* m, const float* X,
                                               const float* T, long long N, float lr,
                                               int update, double* loss, void* stream) {
@@ -667,6 +728,9 @@ void mesh_codec_mlp_destroy(mesh_codec_mlp_t* m) {
   if (m->loss_dev) cudaFree(m->loss_dev);
   if (m->loss_host) cudaFreeHost(m->loss_host);
   if (m->stat_part) cudaFree(m->stat_part);
+  if (m->W2f) cudaFree(m->W2f);
+  if (m->tc_status) cudaFree(m->tc_status);
+  if (m->tc_status_host) cudaFreeHost(m->tc_status_host);
   delete m;
 }
 

@@ -84,7 +84,7 @@ class WarmStart:
         if start == "learned" and self.pos.fitted:
             feat, _ = _c.warm_features(x_last, anc, self.anchors, self.nearest, self.dist, delta,
                                        self.delta_prev)
-            pred = self.pos.net.forward(feat)
+            pred = self.pos.net.infer(feat)
         elif start not in ("previous", "learned"):
             raise ValueError(start)
         return _c.warm_compose(x_last, self.F, pred), delta, anc
@@ -113,7 +113,7 @@ class WarmStart:
         pred = None
         if start == "learned" and self.basis.fitted:
             feat, _ = _c.basis_features(self.U_prev)
-            pred = self.basis.net.forward(feat)
+            pred = self.basis.net.infer(feat)
         elif start not in ("previous", "learned"):
             raise ValueError(start)
         return _c.basis_compose(self.U_prev, pred)

@@ -67,6 +67,26 @@ def _net_with_norm(X, seed=3, check=False):
     return net, (mu, inv)
 
 
+@pytest.mark.parametrize("N,hidden", [(1, 256), (3001, 256), (4194304 + 77, 256), (999, 36)])
+def test_mlp_tensor_core_inference(N, hidden):
+    """infer (hidden-to-hidden product as a TF32 GEMM) against forward (FP32
+    products) and the FP64 oracle: TF32 rounds the activations to a 10-bit
+    mantissa, so the outputs agree to ~1e-3 of their scale."""
+    X, _ = _data(N, seed=N % 1000)
+    net = _c().Mlp(N_IN, hidden, N_OUT, seed=5)
+    net.fit_normalizer(_cuda(X))
+    Xd = _cuda(X)
+    Yf = net.forward(Xd)
+    Yi = net.infer(Xd)
+    scale = max(float(Yf.abs().max()), 1e-3)
+    assert float((Yi - Yf).abs().max()) <= 2e-3 * scale
+    if N <= 3001:
+        w = net.params(0).cpu().numpy()
+        norm = tuple(t.cpu().numpy() for t in net.normalizer())
+        Yo = omlp.forward(w, X, N_IN, hidden, N_OUT, weight_round="bf16", norm=norm)
+        assert np.max(np.abs(Yi.cpu().numpy() - Yo)) <= 2e-3 * max(np.max(np.abs(Yo)), 1e-3)
+
+
 @pytest.mark.parametrize("N", [1, 3001])
 def test_mlp_normalizer_and_forward(N):
     X, _ = _data(N, seed=N)
