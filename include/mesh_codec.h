@@ -494,7 +494,8 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_mlp_forward(mesh_codec_mlp_t* m, c
  * accumulate in float32.  Outputs agree with mesh_codec_mlp_forward to
  * about 1e-3 of their scale.  For predictions over many rows (the warm
  * start's first iterate); training and the gradient checks use the
- * float32-product forward.  Synchronises `stream` to read the tensor-core
+ * float32-product forward.  It uses the bfloat16 weights whatever the check
+ * mode (mesh_codec_mlp_set_check_mode).  Synchronises `stream` to read the tensor-core
  * status; when n_hidden is not a multiple of 4 (no TMA description) it runs
  * mesh_codec_mlp_forward.  Errors: MC_E_INVALID_ARG, MC_E_OOM, MC_E_CUDA. */
 MESH_CODEC_API mesh_codec_status_t mesh_codec_mlp_infer(mesh_codec_mlp_t* m, const float* X,
