@@ -47,6 +47,29 @@ def test_anchored_ls_matches_dense_least_squares():
     assert np.linalg.norm(res) <= 1e-13 * np.linalg.norm(b)
 
 
+def test_factored_form_equals_the_frames_solve():
+    # The decoder's factored form (Eq. 12 reassociated): with M = L^T L + P^T P,
+    # M Y = L^T C'^T and M G = P^T, the frames solution is X = Y U'^T + G A^.
+    tris, pos = _tiny(level=2, F=20)
+    n = pos.shape[1]
+    rp, ci, dg = graph.build_adjacency(tris, n)
+    anchors = codec.select_anchors(n, 5, 2)
+    r = np.random.default_rng(8)
+    k, F = 4, 20
+    U = np.linalg.qr(r.normal(size=(F, k)))[0]          # dictionary, F x k
+    C = r.normal(size=(k, n))                            # coefficients
+    A = r.normal(size=(anchors.size, F))                 # anchor trajectories
+    X, _, M = codec.solve_anchored_ls(rp, ci, dg, anchors, (U @ C).T, A)
+    Mf = M.toarray()
+    Y = np.linalg.solve(Mf, graph.apply_laplacian_transpose(rp, ci, dg, C.T))
+    Pt = np.zeros((n, anchors.size))
+    Pt[anchors, np.arange(anchors.size)] = 1.0
+    G = np.linalg.solve(Mf, Pt)
+    np.testing.assert_allclose(Y @ U.T + G @ A, X, atol=1e-9 * np.abs(X).max())
+    # M 1 = P^T 1 (L 1 = 0), so every row of the anchor response sums to one
+    np.testing.assert_allclose(G.sum(axis=1), 1.0, atol=1e-9)
+
+
 def test_consistent_system_returns_exact_solution():
     v, tris = icosphere(2)
     n = v.shape[0]
