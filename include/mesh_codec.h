@@ -55,8 +55,25 @@ typedef enum mesh_codec_status {
                                     input, or F above ~28,000 with rank-deficient data);
                                     numerically rank-deficient trajectories are completed,
                                     not rejected */
-    MC_E_BAD_ANCHORS = 10        /* caller-supplied anchors not strictly increasing in [0, n) */
+    MC_E_BAD_ANCHORS = 10,       /* caller-supplied anchors not strictly increasing in [0, n) */
+    MC_E_NO_ANCHOR_IN_COMPONENT = 11, /* a connected component of the mesh holds no anchor:
+                                    L 1 = 0 on every component (Eq. 3), so L^T L + P^T P
+                                    of Eq. 12 is singular there; nothing is solved */
+    MC_E_TIMEOUT = 12            /* a bounded wait inside a tensor-core kernel ran out
+                                    (mesh_codec_set_wait_limit); the kernel drained its
+                                    copies, freed its tensor memory and returned; the
+                                    results of that call are not valid */
 } mesh_codec_status_t;
+
+/* Layout of the positions at the boundary (encode input, decode output,
+ * the decoder's first iterate). */
+typedef enum mesh_codec_layout {
+    MC_LAYOUT_FRAMES = 0,        /* float64 [F][n][3]: frame-major, the sequence
+                                    A = [M_1; ...; M_F] of Section II */
+    MC_LAYOUT_VERTEX_MAJOR = 1   /* float64 [n][3][F]: one row of 3F values per vertex,
+                                    coordinate c of frame f at column c*F + f (the
+                                    codec's internal layout, so no transpose is run) */
+} mesh_codec_layout_t;
 
 /* Precision of the encoder's dense products and of the decoder's solve. */
 typedef enum mesh_codec_precision {
@@ -112,8 +129,15 @@ typedef struct mesh_codec_params {
                                     r in 1..12 = iterative refinement: the residual of Eq. 12's
                                     normal equations in FP64, FP32 CG corrections solved to a
                                     relative 10^-r, until every column's FP64 residual meets
-                                    cg_rtol (FP64 accuracy from FP32 sweeps, any precision) */
-    int32_t reserved[2];         /* must be zero */
+                                    cg_rtol (FP64 accuracy from FP32 sweeps, any precision).
+                                    In the TF32 / BF16 modes refine > 0 also keeps the
+                                    projection (Eq. 9), the back-projection (Eq. 11) and the
+                                    decoder's final products in FP64: the tensor cores then
+                                    run only the orthogonal-iteration sweeps, which the FP64
+                                    refinement sweeps and Rayleigh-Ritz correct */
+    int32_t layout;              /* mesh_codec_layout_t of every positions argument; the
+                                    blocks variant needs MC_LAYOUT_FRAMES */
+    int32_t reserved[1];         /* must be zero */
 } mesh_codec_params_t;
 
 typedef struct mesh_codec_stats {
@@ -150,9 +174,13 @@ MESH_CODEC_API void mesh_codec_default_params(mesh_codec_params_t* p);
  *              smallest splitmix64 keys), or int32 [n_c] strictly increasing
  *              indices in [0, n), host or device (`anchors_on_device`).
  * Builds the CSR adjacency, degrees, the anchor set, the starting basis and
- * allocates the device workspace for (n, F, k).  Synchronises `stream`.
+ * allocates the device workspace for (n, F, k).  Labels the connected
+ * components of the mesh; with n_c > 0 every component must hold an anchor
+ * (Eq. 12 is singular otherwise), with n_c = 0 the handle can only encode.
+ * Synchronises `stream`.
  * Errors: MC_E_INVALID_ARG, MC_E_BAD_MESH, MC_E_ISOLATED_VERTEX,
- * MC_E_BAD_ANCHORS, MC_E_OOM, MC_E_CUDA, MC_E_NUMERICAL; *out is NULL then. */
+ * MC_E_BAD_ANCHORS, MC_E_NO_ANCHOR_IN_COMPONENT, MC_E_OOM, MC_E_CUDA,
+ * MC_E_NUMERICAL; *out is NULL then. */
 MESH_CODEC_API mesh_codec_status_t mesh_codec_create(const mesh_codec_params_t* params,
                                       const int32_t* triangles, int triangles_on_device,
                                       const int32_t* anchors, int anchors_on_device,
@@ -179,7 +207,8 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_encoded_size(const mesh_codec_t* h
 
 /* Encoder (Section III, Eq. 7-10).
  *   positions: device float64 [F][n][3] (frame-major, the sequence
- *              A = [M_1; ...; M_F] of Section II).
+ *              A = [M_1; ...; M_F] of Section II), or [n][3][F] with
+ *              params.layout = MC_LAYOUT_VERTEX_MAJOR.
  *   bitstream: device bytes, `capacity` of them, 8-byte aligned; receives
  *              the stream: a 64-byte header ("DMC1", version 1, n, F, k,
  *              n_c, the three bit counts, the Laplacian kind, the total
@@ -193,7 +222,8 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_encoded_size(const mesh_codec_t* h
  *   written:   host; set to the stream size, also on MC_E_BUFFER_TOO_SMALL
  *              (nothing is enqueued then).
  * Synchronises `stream` once at the end to read the device status word.
- * Errors: MC_E_INVALID_ARG, MC_E_BUFFER_TOO_SMALL, MC_E_NUMERICAL, MC_E_CUDA. */
+ * Errors: MC_E_INVALID_ARG, MC_E_BUFFER_TOO_SMALL, MC_E_NUMERICAL,
+ * MC_E_TIMEOUT, MC_E_CUDA. */
 MESH_CODEC_API mesh_codec_status_t mesh_codec_encode(mesh_codec_t* h, const double* positions,
                                       uint8_t* bitstream, size_t capacity, size_t* written,
                                       void* stream);
@@ -201,12 +231,15 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_encode(mesh_codec_t* h, const doub
 /* Decoder (Eq. 11-12, parallel anchored reconstruction over all frames).
  *   bitstream:     device bytes, `bytes` of them, produced by a handle with
  *                  the same parameters and connectivity.
- *   positions_out: device float64 [F][n][3].
- * Reads the 64-byte header back to the host (one synchronisation) and the
- * status word at the end (a second one).  MC_E_NOT_CONVERGED still writes
- * the best iterate.
- * Errors: MC_E_INVALID_ARG, MC_E_BITSTREAM_CORRUPT, MC_E_NOT_CONVERGED,
- * MC_E_CUDA. */
+ *   positions_out: device float64 [F][n][3] (or [n][3][F] with
+ *                  MC_LAYOUT_VERTEX_MAJOR).
+ * Reads the 64-byte header back to the host (one synchronisation), checks
+ * that the stream's anchors hold one vertex of every connected component
+ * (a second one; MC_E_NO_ANCHOR_IN_COMPONENT before any solve work
+ * otherwise) and reads the status word at the end (a third one).
+ * MC_E_NOT_CONVERGED still writes the best iterate.
+ * Errors: MC_E_INVALID_ARG, MC_E_BITSTREAM_CORRUPT,
+ * MC_E_NO_ANCHOR_IN_COMPONENT, MC_E_NOT_CONVERGED, MC_E_TIMEOUT, MC_E_CUDA. */
 MESH_CODEC_API mesh_codec_status_t mesh_codec_decode(mesh_codec_t* h, const uint8_t* bitstream, size_t bytes,
                                       double* positions_out, void* stream);
 
@@ -387,18 +420,30 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_get_profile(const mesh_codec_t* h,
  * [M][K] and [N][K], operands rounded to TF32 (kind 0) or BF16 (kind 1),
  * products accumulated in FP32 on tcgen05 tensor cores per K split, splits
  * summed in FP64.  Allocates and frees its own temporaries; synchronises
- * `stream`.  Errors: MC_E_INVALID_ARG, MC_E_OOM, MC_E_CUDA. */
+ * `stream`.  Errors: MC_E_INVALID_ARG, MC_E_OOM, MC_E_TIMEOUT, MC_E_CUDA. */
 MESH_CODEC_API mesh_codec_status_t mesh_codec_selftest_gemm(int kind, int M, int N, int K,
                                                             int splits, const float* A,
                                                             const float* B, double* C,
                                                             void* stream);
 
+/* Limit, in nanoseconds of the GPU's global timer, on every wait of the
+ * tensor-core kernels (a copy landing in shared memory, the products that
+ * read a stage completing); 0 restores the default of 2 s.  Process-wide;
+ * read when a kernel is launched.  A wait that runs out makes its block
+ * record a timeout, wait (again bounded) for its copies and products in
+ * flight, free its tensor memory and return; the call then reports
+ * MC_E_TIMEOUT and the next call proceeds normally.  A limit of a few
+ * microseconds makes the waits of a long product run out on purpose, which
+ * is how the timeout path is tested.  Errors: none (always MC_OK). */
+MESH_CODEC_API mesh_codec_status_t mesh_codec_set_wait_limit(unsigned long long ns);
+
 /* Adjacency build that allocates nothing.  The paper has no counterpart:
- * this is a service for callers that cannot call cudaMalloc where they
- * need a mesh's adjacency, such as code running while its stream is being
- * captured into a CUDA graph (allocation cannot be captured), real-time
- * hosts that plan every allocation in advance, or plug-ins whose device
- * memory belongs to another framework's allocator.
+ * this is a service for callers that cannot call cudaMalloc where they need
+ * a mesh's adjacency, such as real-time hosts that make every allocation
+ * before their processing loop starts (an allocation can block for
+ * milliseconds and synchronise the device), or plug-ins whose device memory
+ * belongs to another framework's caching allocator (a cudaMalloc of their
+ * own can fail or fragment the pool that framework manages).
  *
  * Builds the same CSR adjacency as mesh_codec_create (MC_BUF_ROW_PTR,
  * MC_BUF_COL_IDX, MC_BUF_DEGREE): every row sorted ascending, duplicates
@@ -419,8 +464,9 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_selftest_gemm(int kind, int M, int
  * keeps the last call's contents; the call clears what must start at zero.
  * Calls whose GPU work overlaps (other host threads, or streams not ordered
  * with this one) race on it and must be serialised by the caller.
- * The first call on each device looks up the array's device address with
- * that device current; make that first call before any stream capture.
+ * The first call on each device (and again in each new CUDA context of that
+ * device, e.g. after cudaDeviceReset) looks up the array's device address
+ * with that device current; make that first call before any stream capture.
  * Synchronises `stream` once (to read nnz and the error word); the
  * compaction of col_idx is enqueued after that and is complete in stream
  * order.  Errors: MC_E_INVALID_ARG, MC_E_BAD_MESH, MC_E_ISOLATED_VERTEX,

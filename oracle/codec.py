@@ -292,9 +292,19 @@ def _factor(M):
                      options={"SymmetricMode": True})
 
 
+def check_anchor_coverage(row_ptr, col_idx, anchors):
+    """Eq. 12 has a unique solution only when every connected component of
+    the mesh holds an anchor; raises graph.AnchorCoverageError otherwise."""
+    bad = graph.uncovered_components(row_ptr, col_idx, anchors)
+    if bad.size:
+        raise graph.AnchorCoverageError(
+            f"{bad.size} connected component(s) without an anchor (first vertex {bad[0]})")
+
+
 def solve_anchored_ls(row_ptr, col_idx, deg, anchors, delta_t, a_hat, kind=0):
     """X minimising ||L X - delta_t||^2 + ||P X - a_hat||^2 (Eq. 12), through
     the normal equations (L^T L + P^T P) X = L^T delta_t + P^T a_hat."""
+    check_anchor_coverage(row_ptr, col_idx, anchors)
     M, L, P = normal_matrix(row_ptr, col_idx, deg, anchors, kind)
     b = graph.apply_laplacian_transpose(row_ptr, col_idx, deg, delta_t, kind)
     b[anchors] += a_hat
@@ -307,6 +317,7 @@ def decode(blob, tris, dict_ref=None):
     d = parse(blob, dict_ref)
     n, F = d["n"], d["F"]
     row_ptr, col_idx, deg = graph.build_adjacency(tris, n)
+    check_anchor_coverage(row_ptr, col_idx, d["anchors"])
     out = np.empty((F, n, 3), dtype=np.float64)
     M, L, P = normal_matrix(row_ptr, col_idx, deg, d["anchors"], d["kind"])
     lu = _factor(M)

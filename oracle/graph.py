@@ -16,10 +16,20 @@ Test infrastructure (see ``oracle/__init__``).
   - kind 1, "combinatorial" (Eq. 1, Eq. 4): L = D - C, delta_i =
     d_i v_i - sum_j v_j (neighbour sum in ascending j, then d_i*v_i minus it).
 
+* Connected components (``components``): the normal matrix L^T L + P^T P
+  of Eq. 12 is singular unless every connected component of the mesh graph
+  holds an anchor (L annihilates the constants of each component, Eq. 3:
+  L 1 = 0 row by row), so the decoder needs one anchor per component.
+  Each vertex is labelled with the smallest vertex index of its component,
+  found by breadth-first search from the lowest unlabelled vertex.
+
 Pinned by: Euler-formula edge counts on closed and open meshes, symmetric
 pattern, degree histograms (icosphere: 12 vertices of degree 5, all others 6;
-torus: all 6), exact zero row sums (tests/test_oracle_graph.py).
+torus: all 6), exact zero row sums, component labels against the null space
+of L and against disjoint unions of meshes (tests/test_oracle_graph.py).
 """
+
+from collections import deque
 
 import numpy as np
 import scipy.sparse as sp
@@ -27,6 +37,10 @@ import scipy.sparse as sp
 
 class MeshError(ValueError):
     """Raised for triangles that do not describe a valid mesh graph."""
+
+
+class AnchorCoverageError(ValueError):
+    """Raised when a connected component holds no anchor (Eq. 12 singular)."""
 
 
 def build_adjacency(tris, n):
@@ -106,3 +120,31 @@ def apply_laplacian_transpose(row_ptr, col_idx, deg, Y, kind=0):
         return apply_laplacian(row_ptr, col_idx, deg, Y, kind=1)
     Wd = Y / deg.astype(np.float64)[:, None]
     return Y - _neighbour_sum(row_ptr, col_idx, Wd)
+
+
+def components(row_ptr, col_idx):
+    """Component label per vertex: the smallest vertex index of its
+    connected component (breadth-first search, one component at a time in
+    ascending order of its lowest vertex)."""
+    n = row_ptr.shape[0] - 1
+    label = np.full(n, -1, dtype=np.int64)
+    for root in range(n):
+        if label[root] >= 0:
+            continue
+        label[root] = root
+        queue = deque([root])
+        while queue:
+            i = queue.popleft()
+            for j in col_idx[row_ptr[i]:row_ptr[i + 1]]:
+                if label[j] < 0:
+                    label[j] = root
+                    queue.append(j)
+    return label.astype(np.int32)
+
+
+def uncovered_components(row_ptr, col_idx, anchors):
+    """Labels (ascending) of the components that hold no anchor."""
+    label = components(row_ptr, col_idx)
+    roots = np.unique(label)
+    covered = np.unique(label[np.asarray(anchors, dtype=np.int64)]) if len(anchors) else []
+    return np.setdiff1d(roots, covered).astype(np.int32)

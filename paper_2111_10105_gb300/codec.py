@@ -19,7 +19,10 @@ STATUS_NAMES = {
     0: "MC_OK", 1: "MC_E_INVALID_ARG", 2: "MC_E_BAD_MESH", 3: "MC_E_ISOLATED_VERTEX",
     4: "MC_E_OOM", 5: "MC_E_CUDA", 6: "MC_E_NOT_CONVERGED", 7: "MC_E_BITSTREAM_CORRUPT",
     8: "MC_E_BUFFER_TOO_SMALL", 9: "MC_E_NUMERICAL", 10: "MC_E_BAD_ANCHORS",
+    11: "MC_E_NO_ANCHOR_IN_COMPONENT", 12: "MC_E_TIMEOUT",
 }
+MC_LAYOUT_FRAMES = 0
+MC_LAYOUT_VERTEX_MAJOR = 1
 MC_PRECISION_FP64 = 0
 MC_PRECISION_TF32 = 1
 MC_PRECISION_BF16 = 2
@@ -44,7 +47,8 @@ class Params(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("solve_mode", ctypes.c_int32),
         ("oi_refine_sweeps", ctypes.c_int32), ("autotune", ctypes.c_int32),
         ("block_delta", ctypes.c_int32), ("block_delta_bits", ctypes.c_int32),
-        ("refine", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
+        ("refine", ctypes.c_int32), ("layout", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 1),
     ]
 
 
@@ -140,6 +144,7 @@ _SIGS = {
     "mesh_codec_destroy": (None, [_P]),
     "mesh_codec_selftest_gemm": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
+    "mesh_codec_set_wait_limit": (ctypes.c_int, [ctypes.c_ulonglong]),
     "mesh_codec_encode_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P]),
     "mesh_codec_decode_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P]),
     "mesh_codec_adjacency_static": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P,
@@ -235,13 +240,17 @@ class MeshCodec:
         _check(lib.mesh_codec_encoded_size(h, ctypes.byref(size)), "mesh_codec_encoded_size")
         self.stream_bytes = size.value
         self.n, self.F, self.k = p.n_vertices, p.n_frames, p.rank
+        # positions at the boundary: [F, n, 3], or [n, 3, F] vertex-major
+        self.pos_shape = ((self.n, 3, self.F) if p.layout == MC_LAYOUT_VERTEX_MAJOR
+                          else (self.F, self.n, 3))
 
     # ------------------------------------------------------------ device API
     def encode(self, positions, out=None, stream=None):
-        """positions: CUDA float64 [F, n, 3] -> CUDA uint8 bitstream."""
+        """positions: CUDA float64 [F, n, 3] ([n, 3, F] with the vertex-major
+        layout) -> CUDA uint8 bitstream."""
         torch = _torch()
         assert positions.is_cuda and positions.dtype == torch.float64
-        assert tuple(positions.shape) == (self.F, self.n, 3) and positions.is_contiguous()
+        assert tuple(positions.shape) == self.pos_shape and positions.is_contiguous()
         if out is None:
             out = torch.empty(self.stream_bytes, dtype=torch.uint8, device=positions.device)
         written = ctypes.c_size_t()
@@ -257,11 +266,11 @@ class MeshCodec:
         torch = _torch()
         assert bitstream.is_cuda and bitstream.dtype == torch.uint8
         if out is None:
-            out = torch.empty((self.F, self.n, 3), dtype=torch.float64, device=bitstream.device)
+            out = torch.empty(self.pos_shape, dtype=torch.float64, device=bitstream.device)
         x0p = None
         if x0 is not None:
             assert x0.is_cuda and x0.dtype == torch.float64 and x0.is_contiguous()
-            assert tuple(x0.shape) == (self.F, self.n, 3)
+            assert tuple(x0.shape) == self.pos_shape
             x0p = ctypes.c_void_p(x0.data_ptr())
         st = self._lib.mesh_codec_decode_ex(self._h, ctypes.c_void_p(bitstream.data_ptr()),
                                             bitstream.numel(), x0p,
@@ -339,7 +348,7 @@ class MeshCodec:
     # ------------------------------------------------------------ host API
     def encode_host(self, positions, out=None, stream=None):
         """positions: numpy / pinned CPU tensor float64 [F, n, 3] -> host bytes."""
-        ptr, keep = _host_ptr(positions, np.float64, (self.F, self.n, 3))
+        ptr, keep = _host_ptr(positions, np.float64, self.pos_shape)
         if out is None:
             out = np.empty(self.stream_bytes, dtype=np.uint8)
         optr, okeep = _host_ptr(out, np.uint8, None)
@@ -353,8 +362,8 @@ class MeshCodec:
     def decode_host(self, bitstream, out=None, stream=None):
         ptr, keep = _host_ptr(bitstream, np.uint8, None)
         if out is None:
-            out = np.empty((self.F, self.n, 3), dtype=np.float64)
-        optr, okeep = _host_ptr(out, np.float64, (self.F, self.n, 3))
+            out = np.empty(self.pos_shape, dtype=np.float64)
+        optr, okeep = _host_ptr(out, np.float64, self.pos_shape)
         nbytes = bitstream.numel() if hasattr(bitstream, "numel") else len(bitstream)
         st = self._lib.mesh_codec_decode_host(self._h, ptr, nbytes, optr, _stream_ptr(stream))
         _check(st, "mesh_codec_decode_host")
@@ -445,6 +454,12 @@ def selftest_gemm(kind, A, B, splits=1, stream=None):
                                         ctypes.c_void_p(C.data_ptr()), _stream_ptr(stream)),
            "mesh_codec_selftest_gemm")
     return C
+
+
+def set_wait_limit(ns=0):
+    """Limit (GPU global-timer nanoseconds) of every wait inside the
+    tensor-core kernels, process-wide; 0 restores the default (2 s)."""
+    _check(load_library().mesh_codec_set_wait_limit(int(ns)), "mesh_codec_set_wait_limit")
 
 
 def _ptr_array(ptrs, ctype=ctypes.c_void_p):

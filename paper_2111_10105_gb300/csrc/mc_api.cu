@@ -51,6 +51,7 @@ size_t carve(mesh_codec* h, void* base) {
   h->row_ptr = c.take<int32_t>(n + 1);
   h->col_idx = c.take<int32_t>(nnz_max);
   h->deg = c.take<int32_t>(n);
+  h->comp = c.take<int32_t>(n);
   h->anchors = c.take<int32_t>(nc);
   h->dec_anchors = c.take<int32_t>(nc);
   h->is_anchor = c.take<uint8_t>(n);
@@ -138,7 +139,9 @@ mesh_codec_status_t status_from_bits(uint32_t bits) {
   if (bits & ST_DEGENERATE) return MC_E_BAD_MESH;
   if (bits & ST_ISOLATED) return MC_E_ISOLATED_VERTEX;
   if (bits & ST_BAD_ANCHORS) return MC_E_BAD_ANCHORS;
+  if (bits & ST_NO_ANCHOR) return MC_E_NO_ANCHOR_IN_COMPONENT;
   if (bits & ST_BITSTREAM) return MC_E_BITSTREAM_CORRUPT;
+  if (bits & ST_TC_TIMEOUT) return MC_E_TIMEOUT;
   if (bits & ST_CHOL_BREAKDOWN) return MC_E_NUMERICAL;
   if (bits & ST_NOT_CONVERGED) return MC_E_NOT_CONVERGED;
   return MC_OK;
@@ -149,6 +152,24 @@ mesh_codec_status_t read_status(mesh_codec* h, cudaStream_t s) {
   MC_TRY(cudaStreamSynchronize(s));
   MC_TRY(cudaGetLastError());
   return status_from_bits(*h->h_status);
+}
+
+// positions in the caller's layout -> the vertex-major [n][3F] matrix: a
+// transpose for [F][n][3] (MC_LAYOUT_FRAMES), a copy for [n][3][F]
+// (MC_LAYOUT_VERTEX_MAJOR), which is the internal layout already
+void ingest(const mesh_codec* h, const double* pos, double* X, cudaStream_t s, Launches& L) {
+  if (h->p.layout == MC_LAYOUT_VERTEX_MAJOR)
+    cudaMemcpyAsync(X, pos, sizeof(double) * 3ull * h->n * h->F, cudaMemcpyDeviceToDevice, s);
+  else
+    frames_to_vertex_major(pos, X, h->F, h->n, s, L);
+}
+
+// the vertex-major [n][3F] matrix -> positions in the caller's layout
+void emit(const mesh_codec* h, const double* X, double* pos, cudaStream_t s, Launches& L) {
+  if (h->p.layout == MC_LAYOUT_VERTEX_MAJOR)
+    cudaMemcpyAsync(pos, X, sizeof(double) * 3ull * h->n * h->F, cudaMemcpyDeviceToDevice, s);
+  else
+    vertex_major_to_frames(X, pos, h->F, h->n, s, L);
 }
 
 bool valid_params(const mesh_codec_params_t* p) {
@@ -172,8 +193,8 @@ bool valid_params(const mesh_codec_params_t* p) {
   if (p->block_delta != 0 && p->block_delta != 1) return false;
   if (p->block_delta_bits < 0 || p->block_delta_bits > MESH_CODEC_MAX_BITS) return false;
   if (p->refine < 0 || p->refine > 12) return false;
-  for (int i = 0; i < 2; ++i)
-    if (p->reserved[i] != 0) return false;
+  if (p->layout != MC_LAYOUT_FRAMES && p->layout != MC_LAYOUT_VERTEX_MAJOR) return false;
+  if (p->reserved[0] != 0) return false;
   return true;
 }
 
@@ -194,6 +215,8 @@ const char* mesh_codec_status_string(mesh_codec_status_t s) {
     case MC_E_BUFFER_TOO_SMALL: return "output buffer too small";
     case MC_E_NUMERICAL: return "no orthonormal basis (non-finite data)";
     case MC_E_BAD_ANCHORS: return "bad anchor indices";
+    case MC_E_NO_ANCHOR_IN_COMPONENT: return "a connected component of the mesh holds no anchor";
+    case MC_E_TIMEOUT: return "a bounded device wait ran out";
   }
   return "unknown status";
 }
@@ -290,6 +313,7 @@ static mesh_codec_status_t create_impl(mesh_codec* h, const int32_t* tris_in, in
     c.take<int32_t>(scan_tmp_elems(n));
     c.take<int32_t>(3ull * T);
     c.take<int32_t>(std::max(h->n_c, 1));
+    c.take<int32_t>(n);
     tmp_bytes = c.off + 256;
   }
   MC_TRY(cudaMalloc(&tmp, tmp_bytes));
@@ -302,6 +326,7 @@ static mesh_codec_status_t create_impl(mesh_codec* h, const int32_t* tris_in, in
   t.scan_tmp = c.take<int32_t>(scan_tmp_elems(n));
   int32_t* tris_dev_buf = c.take<int32_t>(3ull * T);
   int32_t* anchors_tmp = c.take<int32_t>(std::max(h->n_c, 1));
+  int32_t* cc_parent = c.take<int32_t>(n);
   const int32_t* tris = tris_in;
   if (!tris_dev) {
     cudaError_t e = cudaMemcpyAsync(tris_dev_buf, tris_in, sizeof(int32_t) * 3ull * T,
@@ -311,6 +336,7 @@ static mesh_codec_status_t create_impl(mesh_codec* h, const int32_t* tris_in, in
   }
   build_csr(tris, T, n, t, h->row_ptr, nullptr, h->deg, h->d_status, s, L);
   compact_csr(t, h->row_ptr, h->col_idx, n, s, L);
+  component_labels(h->row_ptr, h->col_idx, n, cc_parent, h->comp, s, L);
   // anchors
   if (h->n_c > 0) {
     if (anchors_in) {
@@ -326,6 +352,8 @@ static mesh_codec_status_t create_impl(mesh_codec* h, const int32_t* tris_in, in
     } else {
       select_anchors(n, h->n_c, h->p.seed, h->anchors, s, L);
     }
+    // Eq. 12 needs an anchor in every connected component (is_anchor: scratch here)
+    anchor_coverage(h->comp, n, h->anchors, h->n_c, h->is_anchor, h->d_status, s, L);
   }
   cudaMemsetAsync(h->is_anchor, 0, n, s);
   mark_anchors(h->anchors, h->n_c, h->is_anchor, s, L);
@@ -418,7 +446,7 @@ static void enqueue_encode(mesh_codec* h, const double* positions, uint8_t* out,
   const int n = h->n, F = h->F, k = h->k, W = h->W;
   const EncodeLayout& lay = o.lay ? *o.lay : h->lay;
   cudaMemsetAsync(h->d_status, 0, sizeof(uint32_t), s);
-  frames_to_vertex_major(positions, h->X, F, n, s, L);
+  ingest(h, positions, h->X, s, L);
   laplacian_rows(h->row_ptr, h->col_idx, h->deg, h->X, h->D, n, W, h->kind, s, L);
 
   // orthogonal iterations, three coordinates batched
@@ -479,8 +507,10 @@ static void enqueue_encode(mesh_codec* h, const double* positions, uint8_t* out,
         StridedOut{h->U, k, 1, (long long)F * k}, 1, nullptr, s, L);
   sign_rule(h->U, F, k, s, L);
   }
-  // projection C_c = U_c^T delta_c^T (k x n)
-  if (h->lp >= 0) {
+  // projection C_c = U_c^T delta_c^T (k x n); with the refined solve it stays
+  // FP64, so that only the orthogonal-iteration sweeps (which the FP64
+  // refinement sweep and Rayleigh-Ritz correct) use the tensor cores
+  if (h->lp >= 0 && h->p.refine == 0) {
     mixed_project(h, s, L);
   } else {
     dgemm(k, n, F, 3, Strided{h->U, 1, k, (long long)F * k}, Strided{h->D, 1, W, F},
@@ -670,7 +700,7 @@ static void decode_prepare(mesh_codec* h, const uint8_t* in, cudaStream_t s, Lau
   if (d.factored && h->lp >= 0) d.Wc = (d.Wc + 3) / 4 * 4;
   if (!d.factored) {
     // delta~_c = (U_c' C_c')^T : (n x k)(k x F) into D[:, cF : cF + F]
-    if (h->lp >= 0) {
+    if (h->lp >= 0 && h->p.refine == 0) {
       mixed_backproject(h, s, L);
     } else {
       dgemm(n, F, k, 3, Strided{h->Cdeq, 1, n, (long long)k * n},
@@ -721,12 +751,12 @@ static void decode_prepare(mesh_codec* h, const uint8_t* in, cudaStream_t s, Lau
   if (d.refine) {
     // the refined solve keeps its iterate in FP64 (X), from X0 or zero
     if (x0 && !d.factored)
-      frames_to_vertex_major(x0, h->X, F, n, s, L);
+      ingest(h, x0, h->X, s, L);
     else
       cudaMemsetAsync(h->X, 0, sizeof(double) * (size_t)n * d.Wc, s);
   } else if (x0 && !d.factored) {
     // warm start: the caller's X0 [F][n][3] as the CG's first iterate
-    frames_to_vertex_major(x0, h->D, F, n, s, L);
+    ingest(h, x0, h->D, s, L);
     if (d.single)
       narrow(h->D, (long long)n * W, (float*)h->X, s, L);
     else
@@ -888,7 +918,7 @@ static void decode_finish(mesh_codec* h, double* out, cudaStream_t s, Launches& 
     Xs = h->B;
   }
   if (!d.factored) {
-    vertex_major_to_frames(Xs, out, F, n, s, L);
+    emit(h, Xs, out, s, L);
   } else {
     // X_c = Y_c U_c'^T + G A^_c into D [n][3F]: on the tensor cores in the mixed
     // modes (FP32 solve), in FP64 otherwise (and for the refined solve)
@@ -903,7 +933,7 @@ static void decode_finish(mesh_codec* h, double* out, cudaStream_t s, Launches& 
       dgemm(n, F, h->n_c, 3, Strided{Gp, g_ld, 1, 0},
             Strided{h->Ahat, F, 1, (long long)std::max(h->n_c, 1) * F}, acc, 1, nullptr, s, L);
     }
-    vertex_major_to_frames(h->D, out, F, n, s, L);
+    emit(h, h->D, out, s, L);
     if (d.store) {
       // keep G and its anchors; valid once the decode reports every column converged
       if (!h->Gcache_anchors &&
@@ -934,11 +964,34 @@ static void decode_finish(mesh_codec* h, double* out, cudaStream_t s, Launches& 
   L.add(1);
 }
 
+// The stream's anchor set (its n_c indices right after the 64-byte header,
+// which the caller has checked) must hold an anchor in every connected
+// component of the mesh, or Eq. 12 is singular.  Enqueues the check and the
+// copy of its result word to pinned memory; is_anchor serves as scratch (the
+// decoder rebuilds it from the stream).
+static void enqueue_anchor_check(mesh_codec* h, const uint8_t* in, cudaStream_t s, Launches& L) {
+  uint32_t* word = h->d_status + 2;
+  cudaMemsetAsync(word, 0, sizeof(uint32_t), s);
+  anchor_coverage(h->comp, h->n, reinterpret_cast<const int32_t*>(in + 64), h->n_c, h->is_anchor,
+                  word, s, L);
+  cudaMemcpyAsync(h->h_status + 2, word, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+}
+
+// after the stream of enqueue_anchor_check has been synchronised
+static mesh_codec_status_t anchor_check_result(const mesh_codec* h) {
+  return (h->h_status[2] & ST_NO_ANCHOR) ? MC_E_NO_ANCHOR_IN_COMPONENT : MC_OK;
+}
+
 static mesh_codec_status_t enqueue_decode(mesh_codec* h, const uint8_t* in, double* out,
                                           cudaStream_t s, Launches& L,
                                           const double* x0 = nullptr,
                                           const double* dict_ref = nullptr,
                                           const EncodeLayout* lay = nullptr) {
+  enqueue_anchor_check(h, in, s, L);
+  MC_TRY(cudaStreamSynchronize(s));
+  MC_TRY(cudaGetLastError());
+  const mesh_codec_status_t cov = anchor_check_result(h);
+  if (cov != MC_OK) return cov;
   decode_prepare(h, in, s, L, x0, dict_ref, lay);
   if (h->dec.refine) {
     const mesh_codec_status_t st = decode_refine(h, s, L);
@@ -1007,7 +1060,7 @@ mesh_codec_status_t mesh_codec_decode_stage(mesh_codec_t* h, const uint8_t* bits
   unpack_sections(bitstream, h->lay, h->Udeq, h->Cdeq, h->Ahat, h->dec_anchors, nullptr,
                   h->d_status, s, L);
   if (delta_out) {
-    if (h->lp >= 0) {
+    if (h->lp >= 0 && h->p.refine == 0) {
       mixed_backproject(h, s, L);
     } else {
       dgemm(n, F, k, 3, Strided{h->Cdeq, 1, n, (long long)k * n},
@@ -1092,6 +1145,7 @@ mesh_codec_status_t mesh_codec_encode_blocks(mesh_codec_t* h, const double* posi
                                              size_t* written, void* stream) {
   if (!h || !positions || !out || !written || n_blocks < 1) return MC_E_INVALID_ARG;
   if (((uintptr_t)out & 7) || ((uintptr_t)positions & 7)) return MC_E_INVALID_ARG;
+  if (h->p.layout != MC_LAYOUT_FRAMES) return MC_E_INVALID_ARG;   // blocks are frame ranges
   const BlocksSizes z = blocks_sizes(h, n_blocks);
   *written = (size_t)z.total;
   if (capacity < z.total) return MC_E_BUFFER_TOO_SMALL;
@@ -1150,6 +1204,7 @@ mesh_codec_status_t mesh_codec_decode_blocks(mesh_codec_t* h, const uint8_t* in,
                                              double* positions_out, void* stream) {
   if (!h || !in || !positions_out) return MC_E_INVALID_ARG;
   if (((uintptr_t)in & 7) || ((uintptr_t)positions_out & 7)) return MC_E_INVALID_ARG;
+  if (h->p.layout != MC_LAYOUT_FRAMES) return MC_E_INVALID_ARG;   // blocks are frame ranges
   if (bytes < 64) return MC_E_BITSTREAM_CORRUPT;
   if (h->n_c == 0) return MC_E_INVALID_ARG;   // Eq. 12 needs anchors
   cudaStream_t s = (cudaStream_t)stream;
@@ -1344,13 +1399,25 @@ mesh_codec_status_t mesh_codec_decode_batch(mesh_codec_t* const* handles, int co
     MC_TRY(cudaStreamSynchronize(handles[i]->own));
     st[i] = check_header(handles[i], handles[i]->h_header, bytes[i]);
   }
+  // every stream's anchors cover every component of its mesh (Eq. 12)
+  for (int i = 0; i < count; ++i) {
+    if (st[i] != MC_OK) continue;
+    mesh_codec* h = handles[i];
+    h->launches_decode = 0;
+    Launches L{&h->launches_decode};
+    enqueue_anchor_check(h, bitstreams[i], h->own, L);
+  }
+  for (int i = 0; i < count; ++i) {
+    if (st[i] != MC_OK) continue;
+    MC_TRY(cudaStreamSynchronize(handles[i]->own));
+    st[i] = anchor_check_result(handles[i]);
+  }
   // phase 1 for every sequence, then their CG solves in lockstep chunks
   std::vector<int> active;
   for (int i = 0; i < count; ++i) {
     if (st[i] != MC_OK) continue;
     mesh_codec* h = handles[i];
     h->last_stream = h->own;
-    h->launches_decode = 0;
     Launches L{&h->launches_decode};
     decode_prepare(h, bitstreams[i], h->own, L);
     if (h->dec.refine) {

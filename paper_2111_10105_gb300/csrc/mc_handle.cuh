@@ -28,6 +28,7 @@ struct mesh_codec {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   int32_t *row_ptr, *col_idx, *deg, *anchors, *dec_anchors;
+  int32_t* comp;                   // connected-component label per vertex (smallest index)
   uint8_t* is_anchor;
   double *inv_d, *inv_diag;
   float *inv_d32, *inv_diag32;     // FP32 copies for the mixed-precision CG

@@ -28,6 +28,7 @@ enum : uint32_t {
   ST_NOT_CONVERGED = 1u << 5,
   ST_BITSTREAM = 1u << 6,
   ST_TC_TIMEOUT = 1u << 7,   // a tensor-core GEMM wait ran out (bounded mbarrier wait)
+  ST_NO_ANCHOR = 1u << 8,    // a connected component holds no anchor (Eq. 12 singular)
 };
 
 // splitmix64 (Steele, Lea, Flood 2014): output i of the generator seeded with s.
@@ -68,6 +69,13 @@ void select_anchors(int n, int n_c, uint64_t seed, int32_t* anchors, cudaStream_
                     Launches& L);
 void check_anchors(const int32_t* anchors, int n_c, int n, uint32_t* status, cudaStream_t s,
                    Launches& L);
+// comp[i] = smallest vertex index of i's connected component (parent: [n] scratch)
+void component_labels(const int32_t* row_ptr, const int32_t* col_idx, int n, int32_t* parent,
+                      int32_t* comp, cudaStream_t s, Launches& L);
+// ST_NO_ANCHOR into *status when a component holds none of the n_c anchors
+// (flag: [n] bytes of scratch)
+void anchor_coverage(const int32_t* comp, int n, const int32_t* anchors, int n_c, uint8_t* flag,
+                     uint32_t* status, cudaStream_t s, Launches& L);
 void vertex_scalars_marked(const int32_t* row_ptr, const int32_t* col_idx, const int32_t* deg,
                            const uint8_t* is_anchor, int n, int kind, double* inv_d,
                            double* inv_diag_m, cudaStream_t s, Launches& L);

@@ -1,18 +1,22 @@
 // Adjacency build that allocates nothing (mesh_codec_adjacency_static).
 //
 // Some callers cannot call cudaMalloc at the point where they need a mesh's
-// adjacency: code that runs while its stream is being captured into a CUDA
-// graph (allocation is not a capturable operation), real-time hosts that plan
-// every allocation up front, and plug-ins inside a process whose device
-// memory is owned by another framework's allocator.  For them this entry
-// point builds the same CSR adjacency as mesh_codec_create, with its
-// temporary buffers in a file-scope device array instead of allocated
-// memory.  The caller still provides the triangles and the three outputs.
+// adjacency: real-time hosts that make every allocation before their loop
+// starts (an allocation can block for milliseconds and may synchronise the
+// device), and plug-ins inside a process whose device memory belongs to
+// another framework's caching allocator (a cudaMalloc beside it can fail
+// or fragment the pool that framework manages).  For them this entry point
+// builds the same CSR adjacency as mesh_codec_create, with its temporary
+// buffers in a file-scope device array instead of allocated memory.  The
+// caller still provides the triangles and the three outputs.  The call
+// waits for its stream once, to read the entry count and the error word.
 //
 // The scratch array below is part of the library image: every GPU on which
 // the library is loaded holds it (7,865,344 bytes) until the process exits.
 // All calls share it, so calls whose GPU work overlaps (different host
 // threads, or different streams without ordering between them) race on it.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "mc_internal.cuh"
@@ -39,21 +43,56 @@ static_assert(kScratchBytes == 7865344, "scratch size is documented in mesh_code
 
 __device__ __align__(256) unsigned char g_adjacency_scratch[kScratchBytes];
 
-// Device address of g_adjacency_scratch, looked up once per device with that
-// device current.  In host code the symbol's name is only a host-side handle.
+// Device address of g_adjacency_scratch.  In host code the symbol's name is
+// only a host-side handle; the address is looked up with cudaGetSymbolAddress
+// with the device current, once per device and CUDA context: the module is
+// loaded again in a new context (after cudaDeviceReset, or in another
+// driver-API context on the same device) and the array can then move, so
+// the cache is keyed on the context's unique ID.  Where the driver's context
+// calls cannot be reached, the address is looked up on every call.
 constexpr int kMaxDevices = 256;
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {nullptr};
+unsigned long long g_ctx_id[kMaxDevices] = {0};
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// the current context's unique ID, or 0 when it cannot be read
+unsigned long long current_context_id() {
+  static std::once_flag once;
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = (CtxGetCurrentFn)p;
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = (CtxGetIdFn)p;
+  });
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 mesh_codec_status_t scratch_address(void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return MC_E_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return MC_E_CUDA;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
+  const unsigned long long id = current_context_id();
+  if (id == 0 || !g_addr[dev] || g_ctx_id[dev] != id) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_adjacency_scratch) != cudaSuccess || !p) return MC_E_CUDA;
+    // the lookup made the device's primary context current if none was
     g_addr[dev] = p;
+    g_ctx_id[dev] = id ? id : current_context_id();
   }
   *out = g_addr[dev];
   return MC_OK;

@@ -14,12 +14,15 @@
 // A 4-stage ring of (A, B) chunks of 128 bytes of K per row is guarded by
 // mbarriers (full: TMA bytes landed; empty: the MMAs that read the stage have
 // completed, signalled by tcgen05.commit).  Every wait is bounded by a
-// %globaltimer deadline; on timeout the CTA records an error bit, drains its
-// outstanding copies (bounded), frees its TMEM and returns.
+// %globaltimer deadline (the process-wide limit of mesh_codec_set_wait_limit,
+// 2 s by default); on timeout the CTA records an error bit, waits (bounded)
+// for the copies it issued and for the products already issued to the tensor
+// core, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "mc_internal.cuh"
@@ -31,7 +34,8 @@ constexpr int kBM = 128;
 constexpr int kStages = 4;
 constexpr uint32_t kAtomBytes = 128;            // one swizzled row of K
 constexpr uint32_t kABytes = kBM * kAtomBytes;  // 16 KiB per stage
-constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s: default limit, and the drain's
+std::atomic<unsigned long long> g_wait_ns{0};           // 0: kWaitNs
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -99,6 +103,7 @@ struct Args {
   int out_kind;   // 0 fp32, 1 fp32 rounded to tf32, 2 bf16, 3 fp64, 4 fp64 added to out
   long long s0, s1, sb, split_stride;
   uint32_t* status;
+  unsigned long long wait_ns;   // limit of every pipeline wait
 };
 
 template <int KIND>  // 0: tf32 (4-byte elements), 1: bf16
@@ -113,6 +118,8 @@ __global__ void __launch_bounds__(128, 1) k_umma_tn(const __grid_constant__ CUte
   uint64_t* bars = (uint64_t*)(sB + kStages * b_bytes);  // full[4], empty[4], done
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * kStages + 1);
   int* abort_flag = (int*)(tmem_slot + 1);
+  int* issued_slot = abort_flag + 1;   // chunks whose copies the producer issued
+  int* consumed_slot = abort_flag + 2; // chunks whose products the issuer committed
   const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * kStages,
                  done = full0 + 16 * kStages;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -129,6 +136,8 @@ __global__ void __launch_bounds__(128, 1) k_umma_tn(const __grid_constant__ CUte
     }
     mbar_init(done, 1);
     *abort_flag = 0;
+    *issued_slot = 0;
+    *consumed_slot = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -142,11 +151,12 @@ __global__ void __launch_bounds__(128, 1) k_umma_tn(const __grid_constant__ CUte
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const unsigned long long deadline = gtimer() + kWaitNs;
+  const unsigned long long deadline = gtimer() + a.wait_ns;
 
   if (warp == 0 && lane == 0 && nk > 0) {
     // producer
-    for (int i = 0; i < nk; ++i) {
+    int i = 0;
+    for (; i < nk; ++i) {
       const int s = i % kStages;
       if (i >= kStages) {
         if (!mbar_wait(empty0 + 8 * s, ((i / kStages) - 1) & 1, deadline)) {
@@ -160,10 +170,12 @@ __global__ void __launch_bounds__(128, 1) k_umma_tn(const __grid_constant__ CUte
       tma_load_3d(smem_u32(sA + s * kABytes), &tmA, kel, m0, b, full0 + 8 * s);
       tma_load_3d(smem_u32(sB + s * b_bytes), &tmB, kel, n0, b, full0 + 8 * s);
     }
+    *issued_slot = i;
   } else if (warp == 1 && lane == 0 && nk > 0) {
     // MMA issuer
     const uint32_t idesc = make_idesc(KIND == 0 ? 2 : 1, a.BN);
-    for (int i = 0; i < nk; ++i) {
+    int i = 0;
+    for (; i < nk; ++i) {
       const int s = i % kStages;
       if (!mbar_wait(full0 + 8 * s, (i / kStages) & 1, deadline)) {
         *abort_flag = 1;
@@ -197,10 +209,11 @@ __global__ void __launch_bounds__(128, 1) k_umma_tn(const __grid_constant__ CUte
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done)
         : "memory");
+    *consumed_slot = i;
   }
   __syncwarp();
   // epilogue: every thread owns one accumulator row
-  bool ok = nk > 0 && mbar_wait(done, 0, deadline + kWaitNs);
+  bool ok = nk > 0 && mbar_wait(done, 0, deadline + a.wait_ns);
   ok = __syncthreads_and(ok && !*(volatile int*)abort_flag) != 0;   // CTA-uniform
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {
@@ -244,12 +257,23 @@ __global__ void __launch_bounds__(128, 1) k_umma_tn(const __grid_constant__ CUte
   }
   if (!ok) {
     if (threadIdx.x == 0 && nk > 0) atomicOr(a.status, ST_TC_TIMEOUT);
-    // drain: wait (bounded) for the copies of every stage that was filled
-    if (warp == 0 && lane == 0) {
+    // drain before TMEM and shared memory are released: wait (bounded by the
+    // default limit) for the last copy issued into every stage, and for the
+    // products issued to the tensor core (the issuer committed them all to
+    // `done`, also when it stopped early)
+    if (warp == 0 && lane == 0 && nk > 0) {
       const unsigned long long d2 = gtimer() + kWaitNs;
-      for (int s = 0; s < kStages && s < nk; ++s) {
-        const int last = ((nk - 1 - s) / kStages);
-        mbar_wait(full0 + 8 * s, last & 1, d2);
+      const int issued = *(volatile int*)issued_slot;
+      for (int s = 0; s < kStages && s < issued; ++s) {
+        const int last = s + kStages * ((issued - 1 - s) / kStages);   // last chunk in stage s
+        mbar_wait(full0 + 8 * s, (last / kStages) & 1, d2);
+      }
+      mbar_wait(done, 0, d2);
+      // and for the arrivals of the per-stage commits of the products
+      const int consumed = *(volatile int*)consumed_slot;
+      for (int s = 0; s < kStages && s < consumed; ++s) {
+        const int last = s + kStages * ((consumed - 1 - s) / kStages);
+        mbar_wait(empty0 + 8 * s, (last / kStages) & 1, d2);
       }
     }
   }
@@ -326,6 +350,8 @@ int umma_tn(int kind, const void* mapA, const void* mapB, int M, int N, int K, i
   a.splits = (a.total_chunks + a.chunks_per_split - 1) / a.chunks_per_split;
   a.out = out; a.out_kind = out_kind; a.s0 = s0; a.s1 = s1; a.sb = sb; a.split_stride = split_stride;
   a.status = status;
+  const unsigned long long lim = tc::g_wait_ns.load(std::memory_order_relaxed);
+  a.wait_ns = lim ? lim : tc::kWaitNs;
   const size_t sm = tc_smem_bytes(BN);
   dim3 grid((N + BN - 1) / BN, (M + tc::kBM - 1) / tc::kBM, batch * a.splits);
   const CUtensorMap& ma = *(const CUtensorMap*)mapA;
@@ -412,6 +438,11 @@ void sum_splits(const float* part, int splits, long long stride, long long count
 // ------------------------------------------------------------ self test
 using namespace mc;
 
+extern "C" mesh_codec_status_t mesh_codec_set_wait_limit(unsigned long long ns) {
+  tc::g_wait_ns.store(ns, std::memory_order_relaxed);
+  return MC_OK;
+}
+
 extern "C" mesh_codec_status_t mesh_codec_selftest_gemm(int kind, int M, int N, int K,
                                                         int splits, const float* A,
                                                         const float* B, double* C,
@@ -450,6 +481,8 @@ extern "C" mesh_codec_status_t mesh_codec_selftest_gemm(int kind, int M, int N, 
     if (cudaMemcpyAsync(&bits, status, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
       st = MC_E_CUDA;
+    else if (bits & ST_TC_TIMEOUT)
+      st = MC_E_TIMEOUT;
     else if (bits)
       st = MC_E_CUDA;
   }

@@ -107,3 +107,17 @@ def open_grid(nx, ny):
     tris = np.concatenate(
         [np.stack([v00, v10, v11], 1), np.stack([v00, v11, v01], 1)], 0)
     return verts, tris.astype(np.int32)
+
+
+def disjoint_union(meshes, offsets=None):
+    """Several meshes as one vertex set with several connected components:
+    the vertices of mesh m follow those of meshes 0..m-1 (translated by
+    offsets[m], a 3-vector, when given) and its triangle indices are shifted
+    by the vertex count before it."""
+    verts, tris, base = [], [], 0
+    for m, (v, t) in enumerate(meshes):
+        shift = np.zeros(3) if offsets is None else np.asarray(offsets[m], dtype=np.float64)
+        verts.append(np.asarray(v, dtype=np.float64) + shift)
+        tris.append(np.asarray(t, dtype=np.int64) + base)
+        base += v.shape[0]
+    return np.concatenate(verts, 0), np.concatenate(tris, 0).astype(np.int32)

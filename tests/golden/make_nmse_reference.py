@@ -25,6 +25,8 @@ WORKLOADS = {
     "icosphere4_F64_k16:farthest": 30,
     "torus200x100_F256_k32:farthest": 30,
     "grid316_F512_k64:farthest": 30,
+    "grid512_F300_k64": 30,
+    "grid512_F300_k64:farthest": 30,
 }
 OUT = os.path.join(HERE, "nmse_reference.txt")
 

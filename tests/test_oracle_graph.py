@@ -119,3 +119,65 @@ def test_random_walk_delta_is_vertex_minus_neighbour_mean():
 def test_rejects_invalid_meshes(tris, n, msg):
     with pytest.raises(MeshError, match=msg):
         graph.build_adjacency(np.array(tris, dtype=np.int32), n)
+
+
+# ---------------------------------------------------------------- components
+def test_components_of_a_disjoint_union_are_its_pieces():
+    from synth import disjoint_union
+    pieces = [icosphere(1), torus_grid(6, 4), icosphere(0), open_grid(3, 5)]
+    v, t = disjoint_union(pieces)
+    rp, ci, _ = graph.build_adjacency(t, v.shape[0])
+    lab = graph.components(rp, ci)
+    expect, base = [], 0
+    for pv, _ in pieces:
+        expect += [base] * pv.shape[0]
+        base += pv.shape[0]
+    np.testing.assert_array_equal(lab, np.array(expect))
+
+
+def test_components_match_the_null_space_of_L_and_csgraph():
+    # a shuffled disjoint union: each label is the smallest index of its
+    # piece, the partition equals scipy's connected components, and each
+    # component's indicator vector spans the null space of L (L 1 = 0 per
+    # component, Eq. 3): dim null(L) = number of components
+    from scipy.sparse.csgraph import connected_components
+    from synth import disjoint_union
+    v, t = disjoint_union([icosphere(1), torus_grid(5, 3), open_grid(4, 4)])
+    n = v.shape[0]
+    perm = np.random.default_rng(3).permutation(n)
+    t = perm[t].astype(np.int32)
+    rp, ci, dg = graph.build_adjacency(t, n)
+    lab = graph.components(rp, ci)
+    A = graph.laplacian_matrix(rp, ci, dg) != 0
+    ncomp, ref = connected_components(A, directed=False)
+    assert len(np.unique(lab)) == ncomp == 3
+    for c in range(ncomp):
+        members = np.nonzero(ref == c)[0]
+        assert np.all(lab[members] == members.min())
+    L = graph.laplacian_matrix(rp, ci, dg).toarray()
+    sv = np.linalg.svd(L, compute_uv=False)
+    assert np.sum(sv < 1e-10 * sv.max()) == ncomp
+    for root in np.unique(lab):
+        ind = (lab == root).astype(np.float64)[:, None]
+        assert np.all(graph.apply_laplacian(rp, ci, dg, ind) == 0.0)
+
+
+def test_uncovered_components_and_the_decoder_check():
+    from oracle import codec
+    from oracle.graph import AnchorCoverageError
+    from synth import disjoint_union
+    a, b = icosphere(1), icosphere(1)
+    v, t = disjoint_union([a, b], offsets=[(0, 0, 0), (3, 0, 0)])
+    rp, ci, _ = graph.build_adjacency(t, v.shape[0])
+    n1 = a[0].shape[0]
+    np.testing.assert_array_equal(graph.uncovered_components(rp, ci, [0, 5]), [n1])
+    np.testing.assert_array_equal(graph.uncovered_components(rp, ci, []), [0, n1])
+    assert graph.uncovered_components(rp, ci, [3, n1 + 1]).size == 0
+    F = 6
+    pos = np.repeat(v[None], F, 0) + 0.01 * np.arange(F)[:, None, None]
+    p = codec.Params(n_frames=F, rank=2, n_anchors=2)
+    blob = codec.encode(t, pos, p, anchors=np.array([3, n1 + 1], dtype=np.int32))
+    codec.decode(blob, t)
+    bad = codec.encode(t, pos, p, anchors=np.array([3, 7], dtype=np.int32))
+    with pytest.raises(AnchorCoverageError):
+        codec.decode(bad, t)

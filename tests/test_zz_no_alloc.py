@@ -1,7 +1,10 @@
 """mesh_codec_adjacency_static: the adjacency build for callers that cannot
-allocate device memory (for example while capturing a stream into a CUDA
-graph).  Its result must equal the adjacency that mesh_codec_create builds,
-on consecutive calls that share the library's static scratch array.
+allocate device memory where they need it (real-time hosts that allocate
+everything up front, plug-ins whose device memory belongs to another
+framework's allocator).  Its result must equal the adjacency that
+mesh_codec_create builds, on consecutive calls that share the library's
+static scratch array, at sizes up to its stated limits, and a call must not
+change the device's free memory.
 
 This file is named so that pytest collects it last."""
 
@@ -86,3 +89,41 @@ def test_limits_and_errors(lib):
     assert st == 2
     st, nnz, rp, ci, dg = _static_adjacency(lib, t, n)
     assert st == 0 and nnz == rp[-1]
+
+
+def test_at_the_limits_and_no_device_memory_taken(lib):
+    # a 512 x 256 torus has exactly MAX_V vertices and MAX_T triangles, where
+    # the scratch carve is fullest
+    from synth import torus_grid
+    v, t = torus_grid(512, 256)
+    n = v.shape[0]
+    assert n == MAX_V and t.shape[0] == MAX_T
+    st, nnz, rp, ci, dg = _static_adjacency(lib, t, n)     # first call: address lookup
+    assert st == 0 and nnz == 6 * n
+    rp0, ci0, dg0 = _create_adjacency(t, n)
+    np.testing.assert_array_equal(rp, rp0)
+    np.testing.assert_array_equal(ci, ci0)
+    np.testing.assert_array_equal(dg, dg0)
+    # inputs and outputs are allocated first; the call itself must leave the
+    # device's free memory and torch's allocator untouched
+    tt = torch.from_numpy(np.ascontiguousarray(t, dtype=np.int32)).cuda()
+    row_ptr = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+    col_idx = torch.empty(6 * MAX_T, dtype=torch.int32, device="cuda")
+    deg = torch.empty(n, dtype=torch.int32, device="cuda")
+    nnz_c = ctypes.c_int32(-1)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(2):
+        st = lib.mesh_codec_adjacency_static(
+            ctypes.c_void_p(tt.data_ptr()), MAX_T, n, ctypes.c_void_p(row_ptr.data_ptr()),
+            ctypes.c_void_p(col_idx.data_ptr()), 6 * MAX_T, ctypes.c_void_p(deg.data_ptr()),
+            ctypes.byref(nnz_c), ctypes.c_void_p(stream.cuda_stream))
+        assert st == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0
+    np.testing.assert_array_equal(row_ptr.cpu().numpy(), rp0)
+    np.testing.assert_array_equal(col_idx.cpu().numpy()[:nnz_c.value], ci0)
