@@ -19,7 +19,7 @@ Conventions
   each M_f an n x 3 matrix).
 """
 
-from .meshes import icosphere, torus_grid, open_grid, disjoint_union  # noqa: F401
+from .meshes import icosphere, torus_grid, open_grid, disjoint_union, sub_mesh  # noqa: F401
 from .motion import (  # noqa: F401
     SequenceSpec,
     make_sequence,

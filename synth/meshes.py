@@ -121,3 +121,16 @@ def disjoint_union(meshes, offsets=None):
         tris.append(np.asarray(t, dtype=np.int64) + base)
         base += v.shape[0]
     return np.concatenate(verts, 0), np.concatenate(tris, 0).astype(np.int32)
+
+
+def sub_mesh(tris, keep):
+    """The part of a mesh on the vertices flagged in `keep` (bool [n]): the
+    triangles whose three vertices are all kept, renumbered in the kept
+    vertices' order.  Returns (tris int32 [T', 3], kept vertex indices)."""
+    keep = np.asarray(keep, dtype=bool)
+    idx = np.nonzero(keep)[0]
+    new = np.full(keep.shape[0], -1, dtype=np.int64)
+    new[idx] = np.arange(idx.shape[0])
+    t = np.asarray(tris, dtype=np.int64)
+    t = t[np.all(keep[t], axis=1)]
+    return new[t].astype(np.int32), idx

@@ -84,6 +84,37 @@ def test_stored_oracle_nmse_for_both_anchor_rules():
 
 @pytest.mark.parametrize("rule", ["random", "farthest"])
 def test_oracle_leg_runs_with_either_anchor_rule(rule):
-    res = bench.oracle_sample("icosphere4_F64_k16", 4, repeats=1, anchor_rule=rule)
+    smp = bench.sample_spec("icosphere4_F64_k16", 4, None, rule)
+    res = bench.oracle_sample(smp, repeats=1)
     assert res["F"] == 4 and res["n"] == 2562 and len(res["times"]) == 1
     assert 0.0 <= res["nmse"] < 1.0
+
+
+def test_oracle_leg_on_a_grid_patch():
+    # the bounded sample of the large grid workloads: a corner patch with 1% anchors
+    smp = bench.sample_spec("grid512_F300_k64", 3, 20, "random")
+    res = bench.oracle_sample(smp, repeats=1)
+    assert res["F"] == 3 and res["n"] == 400 and res["n_anchors"] == 4
+    assert "20x20 corner patch" in bench.describe_sample(res, smp)
+
+
+def test_roofline_scales_sampled_kernels_to_graph_iterations():
+    # sampled kernels add up to 7.8 ms per iteration; the graph-replayed runs
+    # took 3.9 ms per iteration: every kernel's time is halved, shares kept
+    prof = {"k_cg_L": (10, 20.0), "k_cg_LT": (10, 30.0), "k_cg_update": (10, 20.0),
+            "k_cg_dir": (10, 5.0), "k_cg_alpha": (10, 1.0), "k_cg_beta": (10, 2.0),
+            "cg_iteration": (300, 1170.0)}
+    stats = {"cg_iters_mean": 100.0, "cg_iters_max": 100}
+    r = bench.roofline(prof, stats, 1000000, 64, 6000000, 10, {"hbm_gbs": 6756.5}, single=True)
+    assert r["kernel"] == "k_cg_LT" and r["cg_iteration_ms"] == pytest.approx(3.9)
+    assert r["mean_launch_ms"] == pytest.approx(1.5) and r["mean_launch_ms_event_bracketed"] == 3.0
+    assert "cg_iteration" not in r["time_share"]
+
+
+def test_workload_forms():
+    # the default workload is the largest single-GPU one, in its benchmark form
+    assert bench.DEFAULT_WORKLOAD == "grid512_F300_k64"
+    f = bench.WORKLOAD_DEFAULTS[bench.DEFAULT_WORKLOAD]
+    assert f["precision"] == "tf32" and f["refine"] > 0
+    sweeps, nmse = bench.nmse_reference("grid512_F300_k64")
+    assert sweeps == bench.SWEEPS and 0.0 < nmse < 1e-8
