@@ -91,7 +91,10 @@ typedef enum mesh_codec_solve_mode {
     MC_SOLVE_FRAMES = 0,         /* one CG column per coordinate and frame (3F columns),
                                     the order of Eq. 11-12 */
     MC_SOLVE_FACTORED = 1,       /* 3k + n_c columns: M Y = L^T C'^T and M G = P^T, then
-                                    X_c = Y_c U_c'^T + G a^_c (same solution, reassociated) */
+                                    X_c = Y_c U_c'^T + G a^_c (same solution, reassociated).
+                                    The TF32 / BF16 modes split a^_c = (a^_c U_c') U_c'^T + E_c:
+                                    Y_c also carries P^T a^_c U_c' and G multiplies only the
+                                    anchors' residual E_c (still the same solution) */
     MC_SOLVE_AUTO = 2            /* FACTORED when 3k + n_c < 3F, or when the stream's
                                     anchors repeat the previous decode's (its anchor
                                     response G is then kept, and later decodes with
@@ -146,7 +149,9 @@ typedef struct mesh_codec_stats {
     int32_t cg_iters_min;
     int32_t cg_columns;          /* number of CG columns solved */
     int32_t cg_not_converged;    /* columns that hit cg_max_iters */
-    int32_t reserved0;
+    int32_t cg_iterations_run;   /* CG iterations the last decode ran over all its columns
+                                    (whole 32-iteration runs; the refined solve's inner
+                                    iterations summed over its outer steps) */
     double oi_change[3];         /* last subspace change per coordinate (0 when not measured) */
     double cg_iters_mean;
     double cg_rel_residual_max;  /* max over columns of ||r|| / ||b|| (recursive residual) */
@@ -342,8 +347,16 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_decode_host(mesh_codec_t* h, const
 /* Batches of independent sequences (each with its own handle, connectivity
  * and sizes).  The work of handle i runs on a stream of its own, forked from
  * and joined back to `stream` with events, so that sequences of uneven size
- * overlap on the GPU; the decoders' CG solves advance in lockstep chunks of
- * 32 iterations.  Arrays have `count` entries; a handle may appear once.
+ * overlap on the GPU.  The decoders' CG solves advance in lockstep runs of
+ * 32 iterations: the FP32 solves whose column count is a multiple of 4 (the
+ * mixed modes' factored solves, frames solves with F % 4 == 0) as one
+ * grouped batch - every phase of an iteration is one launch of a persistent
+ * grid over a work table of (sequence, row block, column tile) items and
+ * (sequence, column) items of all sequences, 32 iterations replayed from one
+ * CUDA graph, finished sequences leaving the table between runs - and the
+ * others each on its own stream.  A grouped sequence's result equals the
+ * result of decoding it alone (same kernels' arithmetic, tile shape and
+ * reduction order).  Arrays have `count` entries; a handle may appear once.
  * `written[i]` / `statuses[i]` (statuses may be NULL) receive the per-
  * sequence results; the return value is the first non-OK status.
  * Synchronises every handle's stream before returning. */
@@ -362,6 +375,18 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_decode_batch(mesh_codec_t* const* 
                                                            double* const* positions_out,
                                                            mesh_codec_status_t* statuses,
                                                            void* stream);
+/* mesh_codec_decode_batch with flags: MC_BATCH_OWN_STREAMS runs every
+ * sequence's CG on its own stream (no grouped batch), the design the grouped
+ * batch is measured against.  Errors: as mesh_codec_decode_batch;
+ * MC_E_INVALID_ARG for unknown flags. */
+#define MC_BATCH_OWN_STREAMS 1
+MESH_CODEC_API mesh_codec_status_t mesh_codec_decode_batch_ex(mesh_codec_t* const* handles,
+                                                              int count,
+                                                              const uint8_t* const* bitstreams,
+                                                              const size_t* bytes,
+                                                              double* const* positions_out,
+                                                              mesh_codec_status_t* statuses,
+                                                              int flags, void* stream);
 
 /* Statistics of the last create / encode / decode (synchronises the handle's
  * last stream). */
@@ -400,9 +425,14 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_copy_buffer(const mesh_codec_t* h,
  * iterations whose first iteration's index is a multiple of `every` samples
  * its last iteration (the 31 before it replay from a CUDA graph, as without
  * timing, and the timed launches queue behind them); shorter runs sample
- * every `every`-th iteration.  Sampling leaves the results unchanged.
- * Either call resets the totals.  mesh_codec_get_profile synchronises the
- * handle's last stream. */
+ * every `every`-th iteration.  The refined solve's inner runs do the same
+ * with direct launches.  The last entry of the profile, "cg_iteration",
+ * holds the whole iterations that ran between one event pair with no
+ * events inside (the 31-iteration graph replays, the first iterations of
+ * each refined run): launches_timed counts those iterations and total_ms
+ * their time, i.e. the iteration time without per-kernel events.
+ * Sampling leaves the results unchanged.  Either call resets the totals.
+ * mesh_codec_get_profile synchronises the handle's last stream. */
 #define MESH_CODEC_PROF_KERNELS 8
 typedef struct mesh_codec_profile {
     int32_t n_kernels;

@@ -56,7 +56,7 @@ class Stats(ctypes.Structure):
     _fields_ = [
         ("oi_sweeps", ctypes.c_int32 * 3), ("cg_iters_max", ctypes.c_int32),
         ("cg_iters_min", ctypes.c_int32), ("cg_columns", ctypes.c_int32),
-        ("cg_not_converged", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("cg_not_converged", ctypes.c_int32), ("cg_iterations_run", ctypes.c_int32),
         ("oi_change", ctypes.c_double * 3), ("cg_iters_mean", ctypes.c_double),
         ("cg_rel_residual_max", ctypes.c_double), ("launches_create", ctypes.c_uint64),
         ("launches_encode", ctypes.c_uint64), ("launches_decode", ctypes.c_uint64),
@@ -147,6 +147,8 @@ _SIGS = {
     "mesh_codec_set_wait_limit": (ctypes.c_int, [ctypes.c_ulonglong]),
     "mesh_codec_encode_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P]),
     "mesh_codec_decode_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P]),
+    "mesh_codec_decode_batch_ex": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, ctypes.c_int,
+                                                  _P]),
     "mesh_codec_adjacency_static": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P,
                                                    ctypes.c_size_t, _P,
                                                    ctypes.POINTER(ctypes.c_int32), _P]),
@@ -492,23 +494,31 @@ def encode_batch(codecs, positions, outs=None, stream=None):
     return [o[: written[i]] for i, o in enumerate(outs)]
 
 
-def decode_batch(codecs, bitstreams, outs=None, stream=None, allow_not_converged=False):
-    """Decode several sequences at once (mesh_codec_decode_batch)."""
+MC_BATCH_OWN_STREAMS = 1
+
+
+def decode_batch(codecs, bitstreams, outs=None, stream=None, allow_not_converged=False,
+                 own_streams=False):
+    """Decode several sequences at once (mesh_codec_decode_batch_ex): the FP32
+    solves as one grouped batch, or with own_streams every sequence's CG on
+    its own stream."""
     torch = _torch()
     lib = load_library()
     count = len(codecs)
     if outs is None:
-        outs = [torch.empty((c.F, c.n, 3), dtype=torch.float64, device="cuda") for c in codecs]
+        outs = [torch.empty(c.pos_shape, dtype=torch.float64, device="cuda") for c in codecs]
     hs = _ptr_array([c._h.value for c in codecs])
     bs = _ptr_array([b.data_ptr() for b in bitstreams])
     nb = _ptr_array([b.numel() for b in bitstreams], ctypes.c_size_t)
     os_ = _ptr_array([o.data_ptr() for o in outs])
     sts = (ctypes.c_int * count)()
-    st = lib.mesh_codec_decode_batch(ctypes.cast(hs, _P), count, ctypes.cast(bs, _P),
-                                     ctypes.cast(nb, _P), ctypes.cast(os_, _P),
-                                     ctypes.cast(sts, _P), _stream_ptr(stream))
+    st = lib.mesh_codec_decode_batch_ex(ctypes.cast(hs, _P), count, ctypes.cast(bs, _P),
+                                        ctypes.cast(nb, _P), ctypes.cast(os_, _P),
+                                        ctypes.cast(sts, _P),
+                                        MC_BATCH_OWN_STREAMS if own_streams else 0,
+                                        _stream_ptr(stream))
     if not (allow_not_converged and st == 6):
-        _check(st, "mesh_codec_decode_batch")
+        _check(st, "mesh_codec_decode_batch_ex")
     return outs
 
 

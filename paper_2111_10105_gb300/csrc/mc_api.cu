@@ -86,6 +86,8 @@ size_t carve(mesh_codec* h, void* base) {
   h->Udeq = c.take<double>(3 * F * k);
   h->Cdeq = c.take<double>(3 * k * n);
   h->Ahat = c.take<double>(3 * nc * F);
+  h->AU = c.take<double>(3 * nc * k);
+  h->Eanc = c.take<double>(3 * nc * F);
   h->Ublk = c.take<double>(3 * F * k);
   h->Uhat = c.take<double>(3 * F * k);
   const size_t Fd = F <= kDirectMaxFrames ? F : 1;
@@ -441,6 +443,26 @@ __global__ void k_axpy_sub(const double* __restrict__ a, const double* __restric
     out[e] = sign > 0 ? __dadd_rn(a[e], b[e]) : __dsub_rn(a[e], b[e]);
 }
 
+// B[anchors[a]][c*k + j] += AU[c][a][j]: P^T (A^_c U'_c) into the data columns
+__global__ void k_scatter_anchor_proj(double* B, const double* __restrict__ AU,
+                                      const int32_t* __restrict__ anchors, int n_c, int k, int Wc) {
+  const long long total = 3LL * n_c * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e / ((long long)n_c * k), rem = e % ((long long)n_c * k);
+    const long long a = rem / k, j = rem % k;
+    B[(long long)anchors[a] * Wc + c * k + j] += AU[e];
+  }
+}
+
+static void scatter_anchor_proj(double* B, const double* AU, const int32_t* anchors, int n_c,
+                                int k, int Wc, cudaStream_t s, Launches& L) {
+  const long long total = 3LL * n_c * k;
+  k_scatter_anchor_proj<<<(int)std::min<long long>((total + 255) / 256, 1024), 256, 0, s>>>(
+      B, AU, anchors, n_c, k, Wc);
+  L.add(1);
+}
+
 static void enqueue_encode(mesh_codec* h, const double* positions, uint8_t* out, cudaStream_t s,
                            Launches& L, bool host_check_tol, const EncodeOpts& o = EncodeOpts()) {
   const int n = h->n, F = h->F, k = h->k, W = h->W;
@@ -583,8 +605,32 @@ static cudaEvent_t* prof_group(mesh_codec* h, int it) {
   return &h->prof_events[(h->prof_used++) * G];
 }
 
+// an event pair around a run of `iters` CG iterations when timing is on, else null
+static cudaEvent_t* prof_run(mesh_codec* h, int iters) {
+  if (h->prof_every <= 0) return nullptr;
+  if ((h->run_used + 1) * 2 > h->run_events.size()) {
+    for (int i = 0; i < 2; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      h->run_events.push_back(e);
+    }
+  }
+  if (h->run_iters.size() < h->run_used + 1) h->run_iters.resize(h->run_used + 1);
+  h->run_iters[h->run_used] = iters;
+  return &h->run_events[(h->run_used++) * 2];
+}
+
 // after the decode's final synchronisation: fold the recorded groups into totals
 static void prof_collect(mesh_codec* h) {
+  for (size_t g = 0; g < h->run_used; ++g) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->run_events[2 * g], h->run_events[2 * g + 1]) ==
+        cudaSuccess) {
+      h->prof_ms[kCgKernels] += ms;
+      h->prof_launches[kCgKernels] += h->run_iters[g];
+    }
+  }
+  h->run_used = 0;
   const size_t G = kCgKernels + 1;
   for (size_t g = 0; g < h->prof_used; ++g) {
     for (int k = 0; k < kCgKernels; ++k) {
@@ -719,6 +765,16 @@ static void decode_prepare(mesh_codec* h, const uint8_t* in, cudaStream_t s, Lau
     laplacian_t_rows(h->row_ptr, h->col_idx, h->deg, h->inv_d, h->D, h->B, n, d.Wc, h->kind, s,
                      L);
     if (!d.cached) unit_anchor_columns(h->B, h->dec_anchors, h->n_c, d.Wc, 3 * k, s, L);
+    if (h->lp >= 0 && h->n_c > 0) {
+      // mixed modes: A^_c = (A^_c U'_c) U'_c^T + E_c, so the data columns also
+      // carry P^T A^_c U'_c and G multiplies only the small residual E_c (the
+      // part of the anchors' trajectories outside the dictionary), which the
+      // tensor cores then form with an error relative to E_c, not to A^_c
+      const long long nc = h->n_c;
+      dgemm((int)nc, k, F, 3, Strided{h->Ahat, F, 1, nc * F}, Strided{h->Udeq, k, 1, (long long)F * k},
+            StridedOut{h->AU, k, 1, nc * k}, 1, nullptr, s, L);
+      scatter_anchor_proj(h->B, h->AU, h->dec_anchors, h->n_c, k, d.Wc, s, L);
+    }
   }
   // CG: FP64 vectors, or FP32 vectors with FP64-accurate dot products in the mixed modes
   // and for the corrections of the refined solve
@@ -824,8 +880,12 @@ static bool decode_cg_chunk(mesh_codec* h, int m, cudaStream_t s, Launches& L) {
   } else if (m == kCgChunk && h->prof_every > 0 && chunk_graph(h, 1, kCgChunk - 1)) {
     // the chunk's timed iteration comes last: its launches queue behind the
     // graph, so no idle gap after the host's convergence check enters its
-    // first kernel (the chunk is chosen by its first iteration's index)
+    // first kernel (the chunk is chosen by its first iteration's index); the
+    // graph itself is bracketed by one event pair (its iterations' time)
+    cudaEvent_t* run = prof_run(h, kCgChunk - 1);
+    if (run) cudaEventRecord(run[0], s);
     cudaGraphLaunch(h->graph_exec[1], s);
+    if (run) cudaEventRecord(run[1], s);
     L.add(6 * (kCgChunk - 1));
     cg_iteration(d.geom, h->row_ptr, h->col_idx, h->deg, d.inv_d, h->is_anchor, d.inv_diag,
                  h->kind, h->X, h->R, h->P, h->Tv, h->Qv, h->p.cg_rtol, h->p.cg_max_iters, h->cg,
@@ -887,10 +947,18 @@ static mesh_codec_status_t decode_refine(mesh_codec* h, cudaStream_t s, Launches
     cg_init(d.geom, Rres, X32, R32, P32, d.inv_diag, h->cg, 1, s, L);
     for (int it = 0; it < inner_max; it += kCgChunk) {
       const int m = std::min(kCgChunk, inner_max - it);
-      for (int j = 0; j < m; ++j, ++d.it)
+      // timing: the first m - 1 iterations as one run, the last one per kernel
+      // (sampled when the run's first iteration index is a multiple of `every`)
+      cudaEvent_t* run = m > 1 ? prof_run(h, m - 1) : nullptr;
+      if (run) cudaEventRecord(run[0], s);
+      const int it0 = d.it;
+      for (int j = 0; j < m; ++j, ++d.it) {
+        const bool last = j == m - 1;
         cg_iteration(d.geom, h->row_ptr, h->col_idx, h->deg, d.inv_d, h->is_anchor, d.inv_diag,
                      h->kind, X32, R32, P32, T32, Q32, inner_rtol, inner_max, h->cg, 1, s, L,
-                     prof_group(h, d.it));
+                     last ? prof_group(h, it0) : nullptr);
+        if (run && j == m - 2) cudaEventRecord(run[1], s);
+      }
       MC_TRY(cudaMemcpyAsync(h->h_active, h->cg.active, sizeof(int32_t),
                              cudaMemcpyDeviceToHost, s));
       MC_TRY(cudaStreamSynchronize(s));
@@ -924,14 +992,41 @@ static void decode_finish(mesh_codec* h, double* out, cudaStream_t s, Launches& 
     // modes (FP32 solve), in FP64 otherwise (and for the refined solve)
     const double* Gp = d.cached ? h->Gcache : Xs + 3 * k;
     const long long g_ld = d.cached ? h->n_c : d.Wc;
-    const bool tc = d.single && !d.refine && h->lp >= 0 && mixed_finish(h, Xs, d.Wc, Gp, g_ld, s, L);
-    if (!tc) {
+    const long long ncs = std::max(h->n_c, 1);
+    // the anchors' term G A: in the mixed modes A = E_c, the residual of the
+    // anchors' trajectories outside the dictionary (see decode_prepare)
+    const double* Aterm = h->Ahat;
+    if (h->lp >= 0 && h->n_c > 0) {
+      const long long nc = h->n_c;
+      dgemm((int)nc, F, k, 3, Strided{h->AU, k, 1, nc * k}, Strided{h->Udeq, 1, k, (long long)F * k},
+            StridedOut{h->Eanc, F, 1, nc * F}, 1, nullptr, s, L);
+      const long long cnt = 3 * nc * F;
+      k_axpy_sub<<<(int)std::min<long long>((cnt + 255) / 256, 1024), 256, 0, s>>>(
+          h->Ahat, h->Eanc, cnt, -1.0, h->Eanc);
+      L.add(1);
+      Aterm = h->Eanc;
+    }
+    // plain mixed modes: both products on the tensor cores; refined solve: the
+    // data product in FP64, the anchors' residual product on the tensor cores
+    bool data_done = false, anchor_done = false;
+    if (d.single && h->lp >= 0) {
+      if (!d.refine) {
+        data_done = anchor_done = mixed_finish(h, Xs, d.Wc, Gp, g_ld, Aterm, true, s, L);
+      } else {
+        dgemm(n, F, k, 3, Strided{Xs, d.Wc, 1, k}, Strided{h->Udeq, 1, k, (long long)F * k},
+              StridedOut{h->D, W, 1, F}, 1, nullptr, s, L);
+        data_done = true;
+        anchor_done = mixed_finish(h, Xs, d.Wc, Gp, g_ld, Aterm, false, s, L);
+      }
+    }
+    if (!data_done)
       dgemm(n, F, k, 3, Strided{Xs, d.Wc, 1, k}, Strided{h->Udeq, 1, k, (long long)F * k},
             StridedOut{h->D, W, 1, F}, 1, nullptr, s, L);
+    if (!anchor_done) {
       StridedOut acc{h->D, W, 1, F};
       acc.accumulate = 1;
-      dgemm(n, F, h->n_c, 3, Strided{Gp, g_ld, 1, 0},
-            Strided{h->Ahat, F, 1, (long long)std::max(h->n_c, 1) * F}, acc, 1, nullptr, s, L);
+      dgemm(n, F, h->n_c, 3, Strided{Gp, g_ld, 1, 0}, Strided{Aterm, F, 1, ncs * F}, acc, 1,
+            nullptr, s, L);
     }
     emit(h, h->D, out, s, L);
     if (d.store) {
@@ -1319,6 +1414,179 @@ mesh_codec_status_t mesh_codec_decode_host(mesh_codec_t* h, const uint8_t* bitst
 }
 
 // ------------------------------------------------------------ batches
+// Grouped CG of a batch (mesh_codec_decode_batch): the FP32 solves whose
+// column count is a multiple of 4 advance together, each phase of an
+// iteration one launch of a persistent grid over a work table of
+// (solve, row block, column tile) items and (solve, column) items; the
+// table lives in device memory, so one captured graph of 32 iterations
+// serves the whole decode while finished solves leave the table between
+// runs.  Every solve keeps its own geometry, vectors and reduction order,
+// so its result equals the result of decoding it alone.
+__global__ void k_gather_active(const CgSeq* __restrict__ seqs, int n, int32_t* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = *seqs[i].active;
+}
+
+struct GroupedCg {
+  std::vector<mesh_codec*> hs;   // the grouped handles, in table order
+  std::vector<char> live;        // per solve: still iterating
+  char* dbuf = nullptr;          // device: solves, row items, column items, counts, active
+  char* hbuf = nullptr;          // pinned: table staging and the active counts
+  CgSeq* d_seqs = nullptr;
+  int4* d_items = nullptr;
+  int2* d_cols = nullptr;
+  int* d_counts = nullptr;       // [0] row items, [1] column items
+  int32_t* d_act = nullptr;
+  CgSeq* h_seqs = nullptr;
+  int4* h_items = nullptr;
+  int2* h_cols = nullptr;
+  int* h_counts = nullptr;
+  int32_t* h_act = nullptr;
+  int grid_rows = 0, grid_cols = 0;
+  size_t smem = 0;
+  cudaStream_t s = nullptr;      // the grouped solves' stream
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev = nullptr;
+
+  ~GroupedCg() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (ev) cudaEventDestroy(ev);
+    if (dbuf) cudaFree(dbuf);
+    if (hbuf) cudaFreeHost(hbuf);
+  }
+  bool any_live() const {
+    for (char l : live)
+      if (l) return true;
+    return false;
+  }
+  // rebuild the tables of the live solves into pinned memory and upload them on s
+  cudaError_t upload_tables() {
+    int ni = 0, nc = 0;
+    for (size_t q = 0; q < hs.size(); ++q) {
+      if (!live[q]) continue;
+      const CgGeom& g = h_seqs[q].g;
+      const int tiles = (g.W + kGroupCols - 1) / kGroupCols;
+      for (int by = 0; by < g.row_blocks; ++by)
+        for (int bx = 0; bx < tiles; ++bx) h_items[ni++] = make_int4((int)q, by, bx, 0);
+      for (int c = 0; c < g.W; ++c) h_cols[nc++] = make_int2((int)q, c);
+    }
+    h_counts[0] = ni;
+    h_counts[1] = nc;
+    cudaError_t e = cudaMemcpyAsync(d_items, h_items, sizeof(int4) * std::max(ni, 1),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_cols, h_cols, sizeof(int2) * std::max(nc, 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_counts, h_counts, sizeof(int) * 2, cudaMemcpyHostToDevice, s);
+    return e;
+  }
+};
+
+// set up the grouped solves of `hs` (phase 1 done on their own streams)
+static mesh_codec_status_t grouped_setup(GroupedCg& G) {
+  const size_t S = G.hs.size();
+  size_t max_items = 0, max_cols = 0;
+  for (mesh_codec* h : G.hs) {
+    const CgGeom& g = h->dec.geom;
+    max_items += (size_t)g.row_blocks * ((g.W + kGroupCols - 1) / kGroupCols);
+    max_cols += (size_t)g.W;
+    G.smem = std::max(G.smem, cg4_grouped_smem(g));
+  }
+  auto carve = [](size_t& off, size_t bytes) {
+    off = (off + 255) & ~size_t(255);
+    const size_t at = off;
+    off += std::max<size_t>(bytes, 1);
+    return at;
+  };
+  size_t off = 0;
+  const size_t o_seqs = carve(off, sizeof(CgSeq) * S), o_items = carve(off, sizeof(int4) * max_items);
+  const size_t o_cols = carve(off, sizeof(int2) * max_cols), o_counts = carve(off, sizeof(int) * 2);
+  const size_t o_act = carve(off, sizeof(int32_t) * S);
+  MC_TRY(cudaMalloc(&G.dbuf, off));
+  MC_TRY(cudaMallocHost(&G.hbuf, off));
+  G.d_seqs = (CgSeq*)(G.dbuf + o_seqs);   G.h_seqs = (CgSeq*)(G.hbuf + o_seqs);
+  G.d_items = (int4*)(G.dbuf + o_items);  G.h_items = (int4*)(G.hbuf + o_items);
+  G.d_cols = (int2*)(G.dbuf + o_cols);    G.h_cols = (int2*)(G.hbuf + o_cols);
+  G.d_counts = (int*)(G.dbuf + o_counts); G.h_counts = (int*)(G.hbuf + o_counts);
+  G.d_act = (int32_t*)(G.dbuf + o_act);   G.h_act = (int32_t*)(G.hbuf + o_act);
+  for (size_t q = 0; q < S; ++q) {
+    mesh_codec* h = G.hs[q];
+    const DecodeState& d = h->dec;
+    CgSeq& c = G.h_seqs[q];
+    c.g = d.geom;
+    c.row_ptr = h->row_ptr; c.col_idx = h->col_idx; c.deg = h->deg;
+    c.inv_d = (const float*)d.inv_d; c.inv_diag = (const float*)d.inv_diag;
+    c.is_anchor = h->is_anchor;
+    c.X = (float*)h->X; c.R = (float*)h->R; c.P = (float*)h->P; c.T = (float*)h->Tv;
+    c.Q = (float*)h->Qv;
+    c.partials = h->cg.partials; c.rz = h->cg.rz; c.rr = h->cg.rr; c.bb = h->cg.bb;
+    c.alpha = h->cg.alpha; c.beta = h->cg.beta;
+    c.done = h->cg.done; c.iters = h->cg.iters; c.active = h->cg.active;
+    c.kind = h->kind;
+    c.max_iters = h->p.cg_max_iters;
+    c.rtol2 = h->p.cg_rtol * h->p.cg_rtol;
+  }
+  G.live.assign(S, 1);
+  G.s = G.hs[0]->own;
+  MC_TRY(cudaEventCreateWithFlags(&G.ev, cudaEventDisableTiming));
+  // the grouped stream waits for every solve's phase 1
+  for (size_t q = 1; q < S; ++q) {
+    MC_TRY(cudaEventRecord(G.hs[q]->ev_chunk, G.hs[q]->own));
+    MC_TRY(cudaStreamWaitEvent(G.s, G.hs[q]->ev_chunk, 0));
+  }
+  MC_TRY(cudaMemcpyAsync(G.d_seqs, G.h_seqs, sizeof(CgSeq) * S, cudaMemcpyHostToDevice, G.s));
+  MC_TRY(G.upload_tables());
+  // persistent grids: 16 CTAs of 64 threads (row items) / 8 of 256 (columns) per SM
+  G.grid_rows = (int)std::max<size_t>(1, std::min<size_t>(max_items, 152 * 16));
+  G.grid_cols = (int)std::max<size_t>(1, std::min<size_t>(max_cols, 152 * 8));
+  // one graph: 32 iterations, then every solve's active-column count to pinned memory
+  cudaStream_t cap = G.hs[0]->cap;
+  if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MC_E_CUDA;
+  Launches none{nullptr};
+  for (int j = 0; j < kCgChunk; ++j)
+    cg4_grouped_iteration(G.d_seqs, G.d_items, G.d_counts, G.d_cols, G.d_counts + 1, G.grid_rows,
+                          G.grid_cols, G.smem, cap, none);
+  k_gather_active<<<1, 256, 0, cap>>>(G.d_seqs, (int)S, G.d_act);
+  cudaMemcpyAsync(G.h_act, G.d_act, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, cap);
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamEndCapture(cap, &graph) != cudaSuccess || !graph) {
+    cudaGetLastError();
+    return MC_E_CUDA;
+  }
+  const cudaError_t e = cudaGraphInstantiate(&G.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    G.exec = nullptr;
+    return MC_E_CUDA;
+  }
+  return MC_OK;
+}
+
+// one run of 32 grouped iterations, enqueued on the grouped stream
+static mesh_codec_status_t grouped_run(GroupedCg& G) {
+  MC_TRY(cudaGraphLaunch(G.exec, G.s));
+  for (size_t q = 0; q < G.hs.size(); ++q)
+    if (G.live[q]) G.hs[q]->launches_decode += 6 * kCgChunk;
+  MC_TRY(cudaEventRecord(G.ev, G.s));
+  return MC_OK;
+}
+
+// after the run's event: count its iterations, retire finished solves
+static mesh_codec_status_t grouped_retire(GroupedCg& G) {
+  bool changed = false;
+  for (size_t q = 0; q < G.hs.size(); ++q) {
+    if (!G.live[q]) continue;
+    mesh_codec* h = G.hs[q];
+    h->dec.it = std::min(h->dec.it + kCgChunk, h->p.cg_max_iters);
+    if (G.h_act[q] == 0 || h->dec.it >= h->p.cg_max_iters) {
+      G.live[q] = 0;
+      changed = true;
+    }
+  }
+  if (changed && G.any_live()) MC_TRY(G.upload_tables());
+  return MC_OK;
+}
+
 // Each handle runs on its own stream, forked from and joined back to the
 // caller's stream with events, so independent sequences of uneven sizes
 // overlap on the GPU.
@@ -1374,8 +1642,18 @@ mesh_codec_status_t mesh_codec_decode_batch(mesh_codec_t* const* handles, int co
                                             const uint8_t* const* bitstreams,
                                             const size_t* bytes, double* const* positions_out,
                                             mesh_codec_status_t* statuses, void* stream) {
+  return mesh_codec_decode_batch_ex(handles, count, bitstreams, bytes, positions_out, statuses,
+                                    0, stream);
+}
+
+mesh_codec_status_t mesh_codec_decode_batch_ex(mesh_codec_t* const* handles, int count,
+                                               const uint8_t* const* bitstreams,
+                                               const size_t* bytes, double* const* positions_out,
+                                               mesh_codec_status_t* statuses, int flags,
+                                               void* stream) {
   if (!batch_args_ok(handles, count) || !bitstreams || !bytes || !positions_out)
     return MC_E_INVALID_ARG;
+  if (flags & ~MC_BATCH_OWN_STREAMS) return MC_E_INVALID_ARG;
   cudaStream_t s0 = (cudaStream_t)stream;
   MC_TRY(cudaEventRecord(handles[0]->ev_fork, s0));
   std::vector<mesh_codec_status_t> st(count, MC_OK);
@@ -1427,9 +1705,28 @@ mesh_codec_status_t mesh_codec_decode_batch(mesh_codec_t* const* handles, int co
     }
     active.push_back(i);
   }
-  while (!active.empty()) {
+  // FP32 solves with a multiple of 4 columns advance as one grouped batch;
+  // the others (FP64, frames solves of 3F % 4 != 0 columns, kernel timing)
+  // run their own chunks on their own streams alongside
+  GroupedCg grouped;
+  std::vector<int> alone;
+  for (int i : active) {
+    mesh_codec* h = handles[i];
+    if (h->dec.single && !h->dec.refine && h->dec.Wc % 4 == 0 && h->prof_every == 0)
+      grouped.hs.push_back(h);
+    else
+      alone.push_back(i);
+  }
+  if (grouped.hs.size() < 2 || (flags & MC_BATCH_OWN_STREAMS)) {
+    alone = active;
+    grouped.hs.clear();
+  } else {
+    const mesh_codec_status_t gs = grouped_setup(grouped);
+    if (gs != MC_OK) return gs;
+  }
+  while (!alone.empty() || grouped.any_live()) {
     std::vector<int> issued;
-    for (int i : active) {
+    for (int i : alone) {
       mesh_codec* h = handles[i];
       Launches L{&h->launches_decode};
       if (decode_cg_chunk(h, 32, h->own, L)) {
@@ -1437,12 +1734,27 @@ mesh_codec_status_t mesh_codec_decode_batch(mesh_codec_t* const* handles, int co
         issued.push_back(i);
       }
     }
+    const bool group_ran = grouped.any_live();
+    if (group_ran) {
+      const mesh_codec_status_t gs = grouped_run(grouped);
+      if (gs != MC_OK) return gs;
+    }
     std::vector<int> still;
     for (int i : issued) {
       MC_TRY(cudaEventSynchronize(handles[i]->ev_chunk));
       if (*handles[i]->h_active != 0) still.push_back(i);
     }
-    active.swap(still);
+    alone.swap(still);
+    if (group_ran) {
+      MC_TRY(cudaEventSynchronize(grouped.ev));
+      const mesh_codec_status_t gs = grouped_retire(grouped);
+      if (gs != MC_OK) return gs;
+    }
+  }
+  if (!grouped.hs.empty()) {
+    // every grouped handle's stream continues after the grouped solves
+    MC_TRY(cudaEventRecord(grouped.ev, grouped.s));
+    for (mesh_codec* h : grouped.hs) MC_TRY(cudaStreamWaitEvent(h->own, grouped.ev, 0));
   }
   for (int i = 0; i < count; ++i) {
     if (st[i] != MC_OK) continue;
@@ -1469,6 +1781,7 @@ mesh_codec_status_t mesh_codec_set_profiling(mesh_codec_t* h, int every) {
   if (!h || every < 0) return MC_E_INVALID_ARG;
   h->prof_every = every;
   h->prof_used = 0;
+  h->run_used = 0;
   for (int k = 0; k < MESH_CODEC_PROF_KERNELS; ++k) {
     h->prof_ms[k] = 0.0;
     h->prof_launches[k] = 0;
@@ -1481,12 +1794,16 @@ mesh_codec_status_t mesh_codec_get_profile(const mesh_codec_t* hc, mesh_codec_pr
   mesh_codec* h = const_cast<mesh_codec*>(hc);
   MC_TRY(cudaStreamSynchronize(h->last_stream));
   std::memset(out, 0, sizeof(*out));
-  out->n_kernels = kCgKernels;
+  out->n_kernels = kCgKernels + 1;
   for (int k = 0; k < kCgKernels; ++k) {
     std::snprintf(out->name[k], sizeof(out->name[k]), "%s", kCgKernelNames[k]);
     out->launches_timed[k] = h->prof_launches[k];
     out->total_ms[k] = h->prof_ms[k];
   }
+  // whole iterations timed as runs (graph replays), without per-kernel events
+  std::snprintf(out->name[kCgKernels], sizeof(out->name[kCgKernels]), "%s", "cg_iteration");
+  out->launches_timed[kCgKernels] = h->prof_launches[kCgKernels];
+  out->total_ms[kCgKernels] = h->prof_ms[kCgKernels];
   return MC_OK;
 }
 
@@ -1523,6 +1840,7 @@ mesh_codec_status_t mesh_codec_get_stats(const mesh_codec_t* hc, mesh_codec_stat
     st->cg_iters_min = mn;
     st->cg_iters_mean = sum / h->cg_columns;
     st->cg_columns = h->cg_columns;
+    st->cg_iterations_run = h->dec.it;
     st->cg_not_converged = nc;
     st->cg_rel_residual_max = res;
   }

@@ -276,17 +276,24 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_LT(CgGeom g, const int32_t* _
   cta_col_partial(pap.value(), sh, partials, col, g.W, col < g.W);
 }
 
-__global__ void k_cg_alpha(CgGeom g, const double* __restrict__ partials,
-                           const double* __restrict__ rz, double* alpha,
-                           const int32_t* __restrict__ done, int32_t* active) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) *active = 0;
-  const int col = blockIdx.x;   // grid: one CTA per column
+// alpha = rz / pAp for one column (the whole CTA reduces its partials)
+__device__ __forceinline__ void cg_alpha_body(const CgGeom& g, int col,
+                                              const double* __restrict__ partials,
+                                              const double* __restrict__ rz, double* alpha,
+                                              const int32_t* __restrict__ done) {
   double pap = col_sum(partials, g.row_blocks, g.W, col);
   if (threadIdx.x == 0) {
     double a = 0.0;
     if (!done[col] && pap > 0.0) a = rz[col] / pap;
     alpha[col] = a;
   }
+}
+
+__global__ void k_cg_alpha(CgGeom g, const double* __restrict__ partials,
+                           const double* __restrict__ rz, double* alpha,
+                           const int32_t* __restrict__ done, int32_t* active) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *active = 0;
+  cg_alpha_body(g, blockIdx.x, partials, rz, alpha, done);   // grid: one CTA per column
 }
 
 template <typename T>
@@ -322,11 +329,12 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_update(CgGeom g, T* __restric
   cta_col_partial(rr.value(), sh, partials + plane, col, g.W, col < g.W);
 }
 
-__global__ void k_cg_beta(CgGeom g, const double* __restrict__ partials, double* rz,
-                          double* rr_out, const double* __restrict__ bb, double* beta,
-                          int32_t* done, int32_t* iters, double rtol2, int max_iters,
-                          int32_t* active) {
-  const int col = blockIdx.x;   // grid: one CTA per column
+// beta, convergence and the active count for one column
+__device__ __forceinline__ void cg_beta_body(const CgGeom& g, int col,
+                                             const double* __restrict__ partials, double* rz,
+                                             double* rr_out, const double* __restrict__ bb,
+                                             double* beta, int32_t* done, int32_t* iters,
+                                             double rtol2, int max_iters, int32_t* active) {
   const long long plane = (long long)g.row_blocks * g.W;
   double rzn = col_sum(partials, g.row_blocks, g.W, col);
   double rr = col_sum(partials + plane, g.row_blocks, g.W, col);
@@ -350,6 +358,46 @@ __global__ void k_cg_beta(CgGeom g, const double* __restrict__ partials, double*
       atomicAdd(active, 1);
     }
   }
+}
+
+__global__ void k_cg_beta(CgGeom g, const double* __restrict__ partials, double* rz,
+                          double* rr_out, const double* __restrict__ bb, double* beta,
+                          int32_t* done, int32_t* iters, double rtol2, int max_iters,
+                          int32_t* active) {
+  cg_beta_body(g, blockIdx.x, partials, rz, rr_out, bb, beta, done, iters, rtol2, max_iters,
+               active);   // grid: one CTA per column
+}
+
+// the per-column reductions of a grouped batch (see cg4_grouped_iteration):
+// persistent CTAs over the column items {solve, column}
+__global__ void k_cgg_alpha(const CgSeq* __restrict__ seqs, const int2* __restrict__ cols,
+                            const int* __restrict__ n_cols) {
+  const int nc = *n_cols;
+  for (int it = blockIdx.x; it < nc; it += gridDim.x) {
+    const int2 w = cols[it];
+    const CgSeq& q = seqs[w.x];
+    if (w.y == 0 && threadIdx.x == 0) *q.active = 0;
+    cg_alpha_body(q.g, w.y, q.partials, q.rz, q.alpha, q.done);
+  }
+}
+
+__global__ void k_cgg_beta(const CgSeq* __restrict__ seqs, const int2* __restrict__ cols,
+                           const int* __restrict__ n_cols) {
+  const int nc = *n_cols;
+  for (int it = blockIdx.x; it < nc; it += gridDim.x) {
+    const int2 w = cols[it];
+    const CgSeq& q = seqs[w.x];
+    cg_beta_body(q.g, w.y, q.partials, q.rz, q.rr, q.bb, q.beta, q.done, q.iters, q.rtol2,
+                 q.max_iters, q.active);
+  }
+}
+
+void cgg_alpha(const CgSeq* seqs, const int2* cols, const int* n_cols, int grid, cudaStream_t s) {
+  k_cgg_alpha<<<grid, 256, 0, s>>>(seqs, cols, n_cols);
+}
+
+void cgg_beta(const CgSeq* seqs, const int2* cols, const int* n_cols, int grid, cudaStream_t s) {
+  k_cgg_beta<<<grid, 256, 0, s>>>(seqs, cols, n_cols);
 }
 
 template <typename T>

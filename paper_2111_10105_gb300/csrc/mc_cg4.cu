@@ -45,14 +45,14 @@ __device__ __forceinline__ int col_lane() { return threadIdx.x % LANES; }
 template <int LANES>
 __device__ __forceinline__ int row_lane() { return threadIdx.x / LANES; }
 template <int LANES>
-__device__ __forceinline__ int first_col() {
-  return blockIdx.x * (4 * LANES) + col_lane<LANES>() * 4;
+__device__ __forceinline__ int first_col(int bx) {
+  return bx * (4 * LANES) + col_lane<LANES>() * 4;
 }
 
 // combine the 8 row lanes' partial sums of this CTA's 4 * LANES columns, fixed order
 template <int LANES>
 __device__ __forceinline__ void cta_partials4(const double v[4], double (*sh)[4 * LANES + 1],
-                                              double* out, int W, int col0, bool valid) {
+                                              double* out, int W, int col0, bool valid, int by) {
   const int lane = col_lane<LANES>(), rl = row_lane<LANES>();
 #pragma unroll
   for (int c = 0; c < 4; ++c) sh[rl][lane * 4 + c] = v[c];
@@ -63,7 +63,7 @@ __device__ __forceinline__ void cta_partials4(const double v[4], double (*sh)[4 
       double s = sh[0][lane * 4 + c];
 #pragma unroll
       for (int r = 1; r < kRowLanes; ++r) s += sh[r][lane * 4 + c];
-      out[(long long)blockIdx.y * W + col0 + c] = s;
+      out[(long long)by * W + col0 + c] = s;
     }
   }
   __syncthreads();
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(LANES * kRowLanes) k4_init(CgGeom g, const dou
                                                              const float* __restrict__ inv_diag,
                                                              double* __restrict__ partials) {
   __shared__ double sh[kRowLanes][4 * LANES + 1];
-  const int col0 = first_col<LANES>();
+  const int col0 = first_col<LANES>(blockIdx.x);
   const int rl = row_lane<LANES>();
   const bool valid = col0 < g.W;
   const long long r0 = (long long)blockIdx.y * g.rows_per_block;
@@ -108,10 +108,10 @@ __global__ void __launch_bounds__(LANES * kRowLanes) k4_init(CgGeom g, const dou
   double v[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) v[c] = rz[c].value();
-  cta_partials4<LANES>(v, sh, partials, g.W, col0, valid);
+  cta_partials4<LANES>(v, sh, partials, g.W, col0, valid, blockIdx.y);
 #pragma unroll
   for (int c = 0; c < 4; ++c) v[c] = bb[c].value();
-  cta_partials4<LANES>(v, sh, partials + plane, g.W, col0, valid);
+  cta_partials4<LANES>(v, sh, partials + plane, g.W, col0, valid, blockIdx.y);
 }
 
 // sum of the neighbours' float4 rows, ascending, loaded four rows at a time
@@ -197,21 +197,20 @@ __device__ __forceinline__ CsrSlice stage_csr(const CgGeom& g, const int32_t* __
   return CsrSlice{row_ptr + r0, col_idx};
 }
 
+// T = L P over one (column tile bx, row block by) of the solve
 template <int LANES>
-__global__ void __launch_bounds__(LANES * kRowLanes) k4_L(CgGeom g,
-                                                          const int32_t* __restrict__ row_ptr,
-                                                          const int32_t* __restrict__ col_idx,
-                                                          const int32_t* __restrict__ deg,
-                                                          const float* __restrict__ inv_d,
-                                                          int kind, const float* __restrict__ P,
-                                                          float* __restrict__ T,
-                                                          const int32_t* __restrict__ done) {
-  extern __shared__ int32_t smem_csr[];
-  const int col0 = first_col<LANES>();
+__device__ __forceinline__ void k4_L_body(const CgGeom& g, int bx, int by,
+                                          const int32_t* __restrict__ row_ptr,
+                                          const int32_t* __restrict__ col_idx,
+                                          const int32_t* __restrict__ deg,
+                                          const float* __restrict__ inv_d, int kind,
+                                          const float* __restrict__ P, float* __restrict__ T,
+                                          const int32_t* __restrict__ done, int32_t* smem) {
+  const int col0 = first_col<LANES>(bx);
   const int rl = row_lane<LANES>();
-  const long long r0 = (long long)blockIdx.y * g.rows_per_block;
+  const long long r0 = (long long)by * g.rows_per_block;
   const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
-  const CsrSlice cs = stage_csr(g, row_ptr, col_idx, r0, r1, smem_csr);
+  const CsrSlice cs = stage_csr(g, row_ptr, col_idx, r0, r1, smem);
   if (col0 >= g.W || group_done(done, col0)) return;
   for (long long i = r0 + rl; i < r1; i += kRowLanes) {
     const float4 s = gather4(P, cs.ci, cs.rp[i - r0], cs.rp[i - r0 + 1], g.W, col0);
@@ -230,26 +229,39 @@ __global__ void __launch_bounds__(LANES * kRowLanes) k4_L(CgGeom g,
 }
 
 template <int LANES>
-__global__ void __launch_bounds__(LANES * kRowLanes) k4_LT(CgGeom g,
-                                                           const int32_t* __restrict__ row_ptr,
-                                                           const int32_t* __restrict__ col_idx,
-                                                           const int32_t* __restrict__ deg,
-                                                           const float* __restrict__ inv_d,
-                                                           int kind,
-                                                           const uint8_t* __restrict__ is_anchor,
-                                                           const float* __restrict__ T,
-                                                           const float* __restrict__ P,
-                                                           float* __restrict__ Q,
-                                                           const int32_t* __restrict__ done,
-                                                           double* __restrict__ partials) {
+__global__ void __launch_bounds__(LANES * kRowLanes) k4_L(CgGeom g,
+                                                          const int32_t* __restrict__ row_ptr,
+                                                          const int32_t* __restrict__ col_idx,
+                                                          const int32_t* __restrict__ deg,
+                                                          const float* __restrict__ inv_d,
+                                                          int kind, const float* __restrict__ P,
+                                                          float* __restrict__ T,
+                                                          const int32_t* __restrict__ done) {
+  extern __shared__ int32_t smem_csr[];
+  k4_L_body<LANES>(g, blockIdx.x, blockIdx.y, row_ptr, col_idx, deg, inv_d, kind, P, T, done,
+                   smem_csr);
+}
+
+// Q = L^T T + [anchor] P and the pAp partials over one (column tile, row block)
+template <int LANES>
+__device__ __forceinline__ void k4_LT_body(const CgGeom& g, int bx, int by,
+                                           const int32_t* __restrict__ row_ptr,
+                                           const int32_t* __restrict__ col_idx,
+                                           const int32_t* __restrict__ deg,
+                                           const float* __restrict__ inv_d, int kind,
+                                           const uint8_t* __restrict__ is_anchor,
+                                           const float* __restrict__ T,
+                                           const float* __restrict__ P, float* __restrict__ Q,
+                                           const int32_t* __restrict__ done,
+                                           double* __restrict__ partials,
+                                           double (*sh)[4 * LANES + 1]) {
   // (the CSR slice stays in global memory here: staging it costs this kernel
   // four registers and an occupancy step, more than the shorter load chain
   // saves; measured on the 99,856-vertex grid)
-  __shared__ double sh[kRowLanes][4 * LANES + 1];
-  const int col0 = first_col<LANES>();
+  const int col0 = first_col<LANES>(bx);
   const int rl = row_lane<LANES>();
   const bool valid = col0 < g.W && !group_done(done, col0);
-  const long long r0 = (long long)blockIdx.y * g.rows_per_block;
+  const long long r0 = (long long)by * g.rows_per_block;
   const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
   Dot2 pap[4];
   if (valid) {
@@ -280,26 +292,42 @@ __global__ void __launch_bounds__(LANES * kRowLanes) k4_LT(CgGeom g,
   double v[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) v[c] = pap[c].value();
-  cta_partials4<LANES>(v, sh, partials, g.W, col0, col0 < g.W);
+  cta_partials4<LANES>(v, sh, partials, g.W, col0, col0 < g.W, by);
 }
 
-// (at most 64 registers: 1,024 resident threads per SM, each with two rows of
-// loads in flight)
 template <int LANES>
-__global__ void __launch_bounds__(LANES * kRowLanes, 1024 / (LANES * kRowLanes))
-    k4_update(CgGeom g, float* __restrict__ X,
-                                                               float* __restrict__ R,
-                                                               const float* __restrict__ P,
-                                                               const float* __restrict__ Q,
-                                                               const float* __restrict__ inv_diag,
-                                                               const double* __restrict__ alpha,
-                                                               const int32_t* __restrict__ done,
-                                                               double* __restrict__ partials) {
+__global__ void __launch_bounds__(LANES * kRowLanes) k4_LT(CgGeom g,
+                                                           const int32_t* __restrict__ row_ptr,
+                                                           const int32_t* __restrict__ col_idx,
+                                                           const int32_t* __restrict__ deg,
+                                                           const float* __restrict__ inv_d,
+                                                           int kind,
+                                                           const uint8_t* __restrict__ is_anchor,
+                                                           const float* __restrict__ T,
+                                                           const float* __restrict__ P,
+                                                           float* __restrict__ Q,
+                                                           const int32_t* __restrict__ done,
+                                                           double* __restrict__ partials) {
   __shared__ double sh[kRowLanes][4 * LANES + 1];
-  const int col0 = first_col<LANES>();
+  k4_LT_body<LANES>(g, blockIdx.x, blockIdx.y, row_ptr, col_idx, deg, inv_d, kind, is_anchor, T,
+                    P, Q, done, partials, sh);
+}
+
+// X += alpha P, R -= alpha Q and the rz / rr partials over one (column tile, row block)
+template <int LANES>
+__device__ __forceinline__ void k4_update_body(const CgGeom& g, int bx, int by,
+                                               float* __restrict__ X, float* __restrict__ R,
+                                               const float* __restrict__ P,
+                                               const float* __restrict__ Q,
+                                               const float* __restrict__ inv_diag,
+                                               const double* __restrict__ alpha,
+                                               const int32_t* __restrict__ done,
+                                               double* __restrict__ partials,
+                                               double (*sh)[4 * LANES + 1]) {
+  const int col0 = first_col<LANES>(bx);
   const int rl = row_lane<LANES>();
   const bool valid = col0 < g.W && !group_done(done, col0);
-  const long long r0 = (long long)blockIdx.y * g.rows_per_block;
+  const long long r0 = (long long)by * g.rows_per_block;
   const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
   Dot2 rz[4], rr[4];
   if (valid) {
@@ -337,24 +365,38 @@ __global__ void __launch_bounds__(LANES * kRowLanes, 1024 / (LANES * kRowLanes))
   double v[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) v[c] = rz[c].value();
-  cta_partials4<LANES>(v, sh, partials, g.W, col0, col0 < g.W);
+  cta_partials4<LANES>(v, sh, partials, g.W, col0, col0 < g.W, by);
 #pragma unroll
   for (int c = 0; c < 4; ++c) v[c] = rr[c].value();
-  cta_partials4<LANES>(v, sh, partials + plane, g.W, col0, col0 < g.W);
+  cta_partials4<LANES>(v, sh, partials + plane, g.W, col0, col0 < g.W, by);
 }
 
+// (at most 64 registers: 1,024 resident threads per SM, each with two rows of
+// loads in flight)
 template <int LANES>
-__global__ void __launch_bounds__(LANES * kRowLanes) k4_dir(CgGeom g, const float* __restrict__ R,
-                                                            float* __restrict__ P,
-                                                            const float* __restrict__ inv_diag,
-                                                            const double* __restrict__ beta,
-                                                            const int32_t* __restrict__ done) {
-  const int col0 = first_col<LANES>();
+__global__ void __launch_bounds__(LANES * kRowLanes, 1024 / (LANES * kRowLanes))
+    k4_update(CgGeom g, float* __restrict__ X, float* __restrict__ R,
+              const float* __restrict__ P, const float* __restrict__ Q,
+              const float* __restrict__ inv_diag, const double* __restrict__ alpha,
+              const int32_t* __restrict__ done, double* __restrict__ partials) {
+  __shared__ double sh[kRowLanes][4 * LANES + 1];
+  k4_update_body<LANES>(g, blockIdx.x, blockIdx.y, X, R, P, Q, inv_diag, alpha, done, partials,
+                        sh);
+}
+
+// P = D^-1 R + beta P over one (column tile, row block)
+template <int LANES>
+__device__ __forceinline__ void k4_dir_body(const CgGeom& g, int bx, int by,
+                                            const float* __restrict__ R, float* __restrict__ P,
+                                            const float* __restrict__ inv_diag,
+                                            const double* __restrict__ beta,
+                                            const int32_t* __restrict__ done) {
+  const int col0 = first_col<LANES>(bx);
   const int rl = row_lane<LANES>();
   if (col0 >= g.W || group_done(done, col0)) return;
   const float b0 = (float)beta[col0], b1 = (float)beta[col0 + 1];
   const float b2 = (float)beta[col0 + 2], b3 = (float)beta[col0 + 3];
-  const long long r0 = (long long)blockIdx.y * g.rows_per_block;
+  const long long r0 = (long long)by * g.rows_per_block;
   const long long r1 = std::min<long long>(g.n, r0 + g.rows_per_block);
   for (long long i = r0 + rl; i < r1; i += kRowLanes) {
     const long long e = i * g.W + col0;
@@ -365,7 +407,92 @@ __global__ void __launch_bounds__(LANES * kRowLanes) k4_dir(CgGeom g, const floa
   }
 }
 
+template <int LANES>
+__global__ void __launch_bounds__(LANES * kRowLanes) k4_dir(CgGeom g, const float* __restrict__ R,
+                                                            float* __restrict__ P,
+                                                            const float* __restrict__ inv_diag,
+                                                            const double* __restrict__ beta,
+                                                            const int32_t* __restrict__ done) {
+  k4_dir_body<LANES>(g, blockIdx.x, blockIdx.y, R, P, inv_diag, beta, done);
+}
+
+// ------------------------------------------------ grouped (work-table) kernels
+// Persistent grids over a table of items: each CTA takes items blockIdx.x,
+// blockIdx.x + gridDim.x, ... and runs the same item body as the per-solve
+// kernels with that solve's geometry and vectors, so every solve of the
+// batch gets the results it gets alone (same row lanes, partials and
+// reduction order).
+constexpr int kGroupLanes = kGroupCols / 4;
+
+__global__ void __launch_bounds__(kGroupLanes * kRowLanes) k4g_L(const CgSeq* __restrict__ seqs,
+                                                                  const int4* __restrict__ items,
+                                                                  const int* __restrict__ n_items) {
+  extern __shared__ int32_t smem_csr[];
+  const int ni = *n_items;
+  for (int it = blockIdx.x; it < ni; it += gridDim.x) {
+    const int4 w = items[it];
+    const CgSeq& q = seqs[w.x];
+    __syncthreads();   // every thread is done with the previous item's CSR slice
+    k4_L_body<kGroupLanes>(q.g, w.z, w.y, q.row_ptr, q.col_idx, q.deg, q.inv_d, q.kind, q.P, q.T,
+                           q.done, smem_csr);
+  }
+}
+
+__global__ void __launch_bounds__(kGroupLanes * kRowLanes) k4g_LT(const CgSeq* __restrict__ seqs,
+                                                                   const int4* __restrict__ items,
+                                                                   const int* __restrict__ n_items) {
+  __shared__ double sh[kRowLanes][4 * kGroupLanes + 1];
+  const int ni = *n_items;
+  for (int it = blockIdx.x; it < ni; it += gridDim.x) {
+    const int4 w = items[it];
+    const CgSeq& q = seqs[w.x];
+    k4_LT_body<kGroupLanes>(q.g, w.z, w.y, q.row_ptr, q.col_idx, q.deg, q.inv_d, q.kind,
+                            q.is_anchor, q.T, q.P, q.Q, q.done, q.partials, sh);
+  }
+}
+
+__global__ void __launch_bounds__(kGroupLanes * kRowLanes, 1024 / (kGroupLanes * kRowLanes))
+    k4g_update(const CgSeq* __restrict__ seqs, const int4* __restrict__ items,
+               const int* __restrict__ n_items) {
+  __shared__ double sh[kRowLanes][4 * kGroupLanes + 1];
+  const int ni = *n_items;
+  for (int it = blockIdx.x; it < ni; it += gridDim.x) {
+    const int4 w = items[it];
+    const CgSeq& q = seqs[w.x];
+    k4_update_body<kGroupLanes>(q.g, w.z, w.y, q.X, q.R, q.P, q.Q, q.inv_diag, q.alpha, q.done,
+                                q.partials, sh);
+  }
+}
+
+__global__ void __launch_bounds__(kGroupLanes * kRowLanes) k4g_dir(const CgSeq* __restrict__ seqs,
+                                                                    const int4* __restrict__ items,
+                                                                    const int* __restrict__ n_items) {
+  const int ni = *n_items;
+  for (int it = blockIdx.x; it < ni; it += gridDim.x) {
+    const int4 w = items[it];
+    const CgSeq& q = seqs[w.x];
+    k4_dir_body<kGroupLanes>(q.g, w.z, w.y, q.R, q.P, q.inv_diag, q.beta, q.done);
+  }
+}
+
 }  // namespace
+
+size_t cg4_grouped_smem(const CgGeom& g) {
+  return g.csr_cap > 0 ? sizeof(int32_t) * (g.rows_per_block + 1 + g.csr_cap) : 0;
+}
+
+void cg4_grouped_iteration(const CgSeq* seqs, const int4* items, const int* n_items,
+                           const int2* cols, const int* n_cols, int grid_rows, int grid_cols,
+                           size_t smem, cudaStream_t s, Launches& L) {
+  constexpr int T = kGroupLanes * kRowLanes;
+  k4g_L<<<grid_rows, T, smem, s>>>(seqs, items, n_items);
+  k4g_LT<<<grid_rows, T, 0, s>>>(seqs, items, n_items);
+  cgg_alpha(seqs, cols, n_cols, grid_cols, s);
+  k4g_update<<<grid_rows, T, 0, s>>>(seqs, items, n_items);
+  cgg_beta(seqs, cols, n_cols, grid_cols, s);
+  k4g_dir<<<grid_rows, T, 0, s>>>(seqs, items, n_items);
+  L.add(6);
+}
 
 // column lanes per CTA for W columns: the fewest idle columns, the widest tile on ties
 static int cg4_lanes(int W) {

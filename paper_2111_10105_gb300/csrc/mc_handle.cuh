@@ -39,6 +39,10 @@ struct mesh_codec {
   double *Cf, *qparams;
   double *X, *D, *B, *R, *P, *Tv, *Qv;
   double *Udeq, *Cdeq, *Ahat;
+  // mixed modes' factored decode: A^_c U'_c [3][n_c][k] (added to the data
+  // columns' right-hand sides at the anchors) and the anchors' residual
+  // E_c = A^_c - (A^_c U'_c) U'_c^T [3][n_c][F] (multiplied by G)
+  double *AU, *Eanc;
   // blocks variant: the previous block's exact basis (Algorithm 1's start)
   // and the decoder's dequantized previous dictionary [3][F][k]; the direct
   // eigendecomposition of R[1] = A A^T: R and V [3][F][F], eigenvalues [3][F]
@@ -80,6 +84,11 @@ struct mesh_codec {
   int prof_every = 0;
   std::vector<cudaEvent_t> prof_events;   // groups of kCgKernels + 1
   size_t prof_used = 0;                    // groups recorded in the current decode
+  // whole runs of CG iterations bracketed by one event pair (no per-kernel
+  // events inside): the iteration time as the CUDA graph replays it
+  std::vector<cudaEvent_t> run_events;     // pairs
+  std::vector<int> run_iters;              // iterations inside each recorded pair
+  size_t run_used = 0;
   int64_t prof_launches[MESH_CODEC_PROF_KERNELS] = {0};
   double prof_ms[MESH_CODEC_PROF_KERNELS] = {0};
   // mixed precision (precision TF32 / BF16): tensor-core operands and maps
@@ -123,5 +132,5 @@ void mixed_oi_sweeps(mesh_codec* h, int sweeps, cudaStream_t s, Launches& L);
 void mixed_project(mesh_codec* h, cudaStream_t s, Launches& L);
 void mixed_backproject(mesh_codec* h, cudaStream_t s, Launches& L);
 bool mixed_finish(mesh_codec* h, const double* Y, long long y_ld, const double* G, long long g_ld,
-                  cudaStream_t s, Launches& L);
+                  const double* A, bool data_product, cudaStream_t s, Launches& L);
 }  // namespace mc

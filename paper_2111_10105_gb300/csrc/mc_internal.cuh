@@ -241,6 +241,30 @@ void cg_init_warm(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_id
                   const void* inv_diag, CgState& st, int single, cudaStream_t s, Launches& L);
 // FP32 CG with four columns per thread (W % 4 == 0), mc_cg4.cu
 bool cg4_applies(int W, int single);
+// One FP32 CG solve (column count a multiple of 4) of a batch whose solves
+// advance together: grouped kernels cover every solve's (row block, column
+// tile) items from a work table in one launch per phase.
+struct CgSeq {
+  CgGeom g;
+  const int32_t *row_ptr, *col_idx, *deg;
+  const float *inv_d, *inv_diag;
+  const uint8_t* is_anchor;
+  float *X, *R, *P, *T, *Q;
+  double *partials, *rz, *rr, *bb, *alpha, *beta;
+  int32_t *done, *iters, *active;
+  int kind, max_iters;
+  double rtol2;
+};
+constexpr int kGroupCols = 32;   // columns per grouped item (8 column lanes x 4)
+// one grouped iteration: row items {solve, row block, column tile, 0}, column
+// items {solve, column}; the counts are read from device memory, so a
+// captured graph of iterations serves a shrinking table
+void cg4_grouped_iteration(const CgSeq* seqs, const int4* items, const int* n_items,
+                           const int2* cols, const int* n_cols, int grid_rows, int grid_cols,
+                           size_t smem, cudaStream_t s, Launches& L);
+void cgg_alpha(const CgSeq* seqs, const int2* cols, const int* n_cols, int grid, cudaStream_t s);
+void cgg_beta(const CgSeq* seqs, const int2* cols, const int* n_cols, int grid, cudaStream_t s);
+size_t cg4_grouped_smem(const CgGeom& g);
 void cg4_init(const CgGeom& g, const double* B, float* X, float* R, float* P,
               const float* inv_diag, double* partials, cudaStream_t s);
 void cg4_op(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* deg,

@@ -7,8 +7,10 @@
 //   then FP64 refinement sweeps and the FP64 Rayleigh-Ritz of the FP64 path;
 //   the projection C_c = U_c^T delta_c^T (Eq. 9) and the decoder's
 //   back-projection delta~_c = (U_c' C_c')^T (Eq. 11) as tensor-core GEMMs;
-//   the factored decoder's X_c = Y_c U_c'^T + G A^_c (Eq. 12 reassociated)
-//   as two tensor-core GEMMs, the second adding onto the first's FP64 result.
+//   the factored decoder's X_c = Y_c U_c'^T + G E_c (Eq. 12 reassociated:
+//   A^_c = (A^_c U'_c) U'_c^T + E_c, the first part solved with the data
+//   columns) as two tensor-core GEMMs, the second adding onto the first's
+//   FP64 result.
 //
 // Operand layouts (all K-major for the TN kernel, padded so that every TMA
 // box starts on a 16-byte boundary; padding is zero):
@@ -156,12 +158,13 @@ void mixed_backproject(mesh_codec* h, cudaStream_t s, Launches& L) {
           h->d_status, s, L);
 }
 
-// X_c = Y_c U_c'^T + G A^_c into D [n][3F] (FP64) on the tensor cores: Y the
+// X_c = Y_c U_c'^T + G A_c into D [n][3F] (FP64) on the tensor cores: Y the
 // 3k data columns of the solve (Y_c at Y + c k, row pitch y_ld), G the anchor
-// response [n][n_c] (row pitch g_ld).  False when the anchor operands cannot
-// be allocated or described; nothing is enqueued then.
+// response [n][n_c] (row pitch g_ld), A [3][n_c][F] the anchors' term; without
+// data_product only G A_c is added onto D.  False when the anchor operands
+// cannot be allocated or described; nothing is enqueued then.
 bool mixed_finish(mesh_codec* h, const double* Y, long long y_ld, const double* G, long long g_ld,
-                  cudaStream_t s, Launches& L) {
+                  const double* A, bool data_product, cudaStream_t s, Launches& L) {
   const long long n = h->n, F = h->F, k = h->k, W = h->W, kp = h->kp, n_c = h->n_c;
   const int eb = lp_bytes(h);
   if (n_c > 0 && !h->Glp) {
@@ -186,16 +189,18 @@ bool mixed_finish(mesh_codec* h, const double* Y, long long y_ld, const double* 
     h->Ahlp = a;
     h->ncp = (int)ncp;
   }
-  // Clp[c][i][r] = Y_c[i][r],  Ulp[c][f][r] = U'_c[f][r]
-  pack_operand_f64(Y, k, y_ld, 1, 3, n, k, kp, kp, n * kp, h->lp, h->Clp, s, L);
-  pack_operand_f64(h->Udeq, F * k, k, 1, 3, F, k, kp, kp, F * kp, h->lp, h->Ulp, s, L);
-  umma_tn(h->lp, h->map_C, h->map_U, (int)n, (int)F, (int)kp, 3, 1, h->D, 3, W, 1, F, 0,
-          h->d_status, s, L);
+  if (data_product) {
+    // Clp[c][i][r] = Y_c[i][r],  Ulp[c][f][r] = U'_c[f][r]
+    pack_operand_f64(Y, k, y_ld, 1, 3, n, k, kp, kp, n * kp, h->lp, h->Clp, s, L);
+    pack_operand_f64(h->Udeq, F * k, k, 1, 3, F, k, kp, kp, F * kp, h->lp, h->Ulp, s, L);
+    umma_tn(h->lp, h->map_C, h->map_U, (int)n, (int)F, (int)kp, 3, 1, h->D, 3, W, 1, F, 0,
+            h->d_status, s, L);
+  }
   if (n_c == 0) return true;
   const long long ncp = h->ncp;
-  // Glp[i][a] = G[i][a],  Ahlp[c][f][a] = A^_c[a][f]
+  // Glp[i][a] = G[i][a],  Ahlp[c][f][a] = A_c[a][f]
   pack_operand_f64(G, 0, g_ld, 1, 1, n, n_c, ncp, ncp, n * ncp, h->lp, h->Glp, s, L);
-  pack_operand_f64(h->Ahat, n_c * F, 1, F, 3, F, n_c, ncp, ncp, F * ncp, h->lp, h->Ahlp, s, L);
+  pack_operand_f64(A, n_c * F, 1, F, 3, F, n_c, ncp, ncp, F * ncp, h->lp, h->Ahlp, s, L);
   for (int c = 0; c < 3; ++c)
     umma_tn(h->lp, h->map_G, h->map_Ah[c], (int)n, (int)F, (int)ncp, 1, 1, h->D + c * F, 4, W,
             1, 0, 0, h->d_status, s, L);

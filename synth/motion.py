@@ -173,6 +173,12 @@ CONFIGS = {
     "grid512_F300_k64": SequenceSpec(
         name="grid512_F300_k64", mesh="grid:512:512", n_frames=300, rank=64,
         n_anchors=2621, seed=1004, n_bumps=4, rigid=False),
+    # the profiling case: the 512 x 512 workload's kind of mesh, motion and
+    # rank (its 192 data columns) at a quarter of its vertices (positions
+    # 403 MB, above the 129 MB L2)
+    "grid256_F256_k64": SequenceSpec(
+        name="grid256_F256_k64", mesh="grid:256:256", n_frames=256, rank=64,
+        n_anchors=655, seed=1005, n_bumps=4, rigid=False),
 }
 
 

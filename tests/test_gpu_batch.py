@@ -66,20 +66,58 @@ def test_batch_equals_single_and_oracle():
         c.close()
 
 
-def test_batch_mixed_autotuned():
+# the mixed batch: the same sequences with k < F throughout (truncation sets
+# their NMSE, so the stated TF32 bound against the oracle applies)
+MIXED = SPECS[:3] + [SequenceSpec(name="d6", mesh="icosphere:2", n_frames=9, rank=6,
+                                  n_anchors=3, seed=14)]
+
+
+def test_batch_mixed_autotuned_against_oracle():
+    from paper_2111_10105_gb300 import MeshCodec
     from paper_2111_10105_gb300.codec import encode_batch, decode_batch
-    seqs = [make_sequence(s) for s in SPECS]
-    cs64 = _codecs(seqs)
-    cs = _codecs(seqs, precision=1, autotune=1)
+    seqs = [make_sequence(s) for s in MIXED]
+    cs = [MeshCodec(tris, pos.shape[1], n_frames=spec.n_frames, rank=spec.rank,
+                    n_anchors=spec.n_anchors, seed=spec.seed, oi_sweeps=25, solve_mode=2,
+                    precision=1, autotune=1, oi_refine_sweeps=1, cg_rtol=1e-6)
+          for spec, (tris, pos) in zip(MIXED, seqs)]
     pos_d = [torch.from_numpy(p).cuda() for _, p in seqs]
-    r64 = decode_batch(cs64, encode_batch(cs64, pos_d))
-    r32 = decode_batch(cs, encode_batch(cs, pos_d))
-    pairs = []
-    for (tris, pos), a, b in zip(seqs, r64, r32):
-        pairs.append((metrics.nmse(pos, a.cpu().numpy()), metrics.nmse(pos, b.cpu().numpy())))
-    # FP32 solve at relative residual 1e-6: an added error of at most 1e-6 of the
-    # centred energy on top of 5% of the FP64 mode's error
-    for ea, eb in pairs:
-        assert abs(eb - ea) <= 0.05 * ea + 1e-6, pairs
-    for c in cs + cs64:
+    bits = encode_batch(cs, pos_d)
+    # two decodes: the automatic solve mode keeps the anchor response on the second
+    for _ in range(2):
+        recs = decode_batch(cs, bits)
+        for spec, (tris, pos), r in zip(MIXED, seqs, recs):
+            p = oc.Params(n_frames=spec.n_frames, rank=spec.rank, n_anchors=spec.n_anchors,
+                          seed=spec.seed, oi_sweeps=25)
+            e_o = metrics.nmse(pos, oc.decode(oc.encode(tris, pos, p), tris))
+            e = metrics.nmse(pos, r.cpu().numpy())
+            assert abs(e - e_o) <= 0.01 * e_o, (spec.name, e, e_o)
+    for c in cs:
+        c.close()
+
+
+def test_grouped_batch_equals_single_decodes():
+    # the FP32 solves of a batch advance as one grouped batch (work-table
+    # kernels over all sequences); every sequence's reconstruction must equal,
+    # to the bit, the one its own handle gives alone, on the first decode
+    # (frames or factored solves) and on the second (kept anchor response)
+    from paper_2111_10105_gb300 import MeshCodec
+    from paper_2111_10105_gb300.codec import encode_batch, decode_batch
+    seqs = [make_sequence(s) for s in MIXED]
+
+    def handles():
+        return [MeshCodec(tris, pos.shape[1], n_frames=spec.n_frames, rank=spec.rank,
+                          n_anchors=spec.n_anchors, seed=spec.seed, oi_sweeps=25, solve_mode=2,
+                          precision=1, autotune=0, oi_refine_sweeps=1, cg_rtol=1e-6)
+                for spec, (tris, pos) in zip(MIXED, seqs)]
+
+    cs, singles = handles(), handles()
+    pos_d = [torch.from_numpy(p).cuda() for _, p in seqs]
+    bits = encode_batch(cs, pos_d)
+    for rnd in range(3):
+        recs = decode_batch(cs, bits)
+        for c, b, r in zip(singles, bits, recs):
+            r1 = c.decode(b)
+            assert torch.equal(r1, r), rnd
+            assert c.stats()["cg_iters_max"] > 0
+    for c in cs + singles:
         c.close()
