@@ -81,7 +81,15 @@ LEARNED_CG_RTOL = 1e-8
 # changed since is to be removed.  The bench scales them by the mean fraction
 # of active columns, as it does the algorithmic bytes.  Which vertices are
 # anchors does not change a launch's data flow (same adjacency and columns).
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    # the 512x512 grid is above the capture size this machine's profiling
+    # rules allow: its k4_update traffic is the 256x256 capture's 23.7 DRAM
+    # bytes per vertex-column entry (1,314 MB over 65,536 x 848 entries, the
+    # algorithmic 24 B) scaled to 262,144 x 192 entries
+    ("grid512_F300_k64", "tf32", 2, 192, "k_cg_update"):
+        (23.67 * 262144 * 192, "profiles/k4_update_L_LT_grid256_F256_k64_tf32.md, "
+                               "per-entry bytes scaled to the 512x512 launch"),
+}
 
 
 # ---------------------------------------------------------------- helpers
