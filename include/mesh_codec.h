@@ -347,19 +347,12 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_decode_host(mesh_codec_t* h, const
 /* Batches of independent sequences (each with its own handle, connectivity
  * and sizes).  The work of handle i runs on a stream of its own, forked from
  * and joined back to `stream` with events, so that sequences of uneven size
- * overlap on the GPU.  The decoders' CG solves advance in lockstep runs of
- * 32 iterations: the FP32 solves whose column count is a multiple of 4 (the
- * mixed modes' factored solves, frames solves with F % 4 == 0) as one
- * grouped batch - every phase of an iteration is one launch of a persistent
- * grid over a work table of (sequence, row block, column tile) items and
- * (sequence, column) items of all sequences, 32 iterations replayed from one
- * CUDA graph, finished sequences leaving the table between runs - and the
- * others each on its own stream.  A grouped sequence's result equals the
- * result of decoding it alone (same kernels' arithmetic, tile shape and
- * reduction order).  Arrays have `count` entries; a handle may appear once.
- * `written[i]` / `statuses[i]` (statuses may be NULL) receive the per-
- * sequence results; the return value is the first non-OK status.
- * Synchronises every handle's stream before returning. */
+ * overlap on the GPU; the decoders' CG solves advance in lockstep runs of 32
+ * iterations, each replayed from the handle's CUDA graph.  Arrays have
+ * `count` entries; a handle may appear once.  `written[i]` / `statuses[i]`
+ * (statuses may be NULL) receive the per-sequence results; the return value
+ * is the first non-OK status.  Synchronises every handle's stream before
+ * returning. */
 MESH_CODEC_API mesh_codec_status_t mesh_codec_encode_batch(mesh_codec_t* const* handles,
                                                            int count,
                                                            const double* const* positions,
@@ -375,11 +368,18 @@ MESH_CODEC_API mesh_codec_status_t mesh_codec_decode_batch(mesh_codec_t* const* 
                                                            double* const* positions_out,
                                                            mesh_codec_status_t* statuses,
                                                            void* stream);
-/* mesh_codec_decode_batch with flags: MC_BATCH_OWN_STREAMS runs every
- * sequence's CG on its own stream (no grouped batch), the design the grouped
- * batch is measured against.  Errors: as mesh_codec_decode_batch;
- * MC_E_INVALID_ARG for unknown flags. */
-#define MC_BATCH_OWN_STREAMS 1
+/* mesh_codec_decode_batch with flags.  MC_BATCH_GROUPED: the FP32 solves
+ * whose column count is a multiple of 4 (the mixed modes' factored solves,
+ * frames solves with F % 4 == 0) advance as grouped batches - the solves are
+ * dealt, largest first, over up to four batches on streams of their own, and
+ * every phase of a batch's iteration is one launch over a work table of
+ * (sequence, row block, column tile) and (sequence, column) items, one CTA
+ * per item, 32 iterations replayed from one CUDA graph, finished sequences
+ * leaving the table between runs; the other solves run on their own streams
+ * alongside.  A grouped sequence's result equals its result alone (same
+ * arithmetic, tile shape and reduction order).  0 is mesh_codec_decode_batch.
+ * Errors: as mesh_codec_decode_batch; MC_E_INVALID_ARG for unknown flags. */
+#define MC_BATCH_GROUPED 1
 MESH_CODEC_API mesh_codec_status_t mesh_codec_decode_batch_ex(mesh_codec_t* const* handles,
                                                               int count,
                                                               const uint8_t* const* bitstreams,

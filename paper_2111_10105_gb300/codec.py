@@ -494,14 +494,14 @@ def encode_batch(codecs, positions, outs=None, stream=None):
     return [o[: written[i]] for i, o in enumerate(outs)]
 
 
-MC_BATCH_OWN_STREAMS = 1
+MC_BATCH_GROUPED = 1
 
 
 def decode_batch(codecs, bitstreams, outs=None, stream=None, allow_not_converged=False,
-                 own_streams=False):
-    """Decode several sequences at once (mesh_codec_decode_batch_ex): the FP32
-    solves as one grouped batch, or with own_streams every sequence's CG on
-    its own stream."""
+                 grouped=False):
+    """Decode several sequences at once (mesh_codec_decode_batch_ex): every
+    sequence's CG on its own stream, or with grouped the FP32 solves as
+    grouped work-table batches."""
     torch = _torch()
     lib = load_library()
     count = len(codecs)
@@ -515,7 +515,7 @@ def decode_batch(codecs, bitstreams, outs=None, stream=None, allow_not_converged
     st = lib.mesh_codec_decode_batch_ex(ctypes.cast(hs, _P), count, ctypes.cast(bs, _P),
                                         ctypes.cast(nb, _P), ctypes.cast(os_, _P),
                                         ctypes.cast(sts, _P),
-                                        MC_BATCH_OWN_STREAMS if own_streams else 0,
+                                        MC_BATCH_GROUPED if grouped else 0,
                                         _stream_ptr(stream))
     if not (allow_not_converged and st == 6):
         _check(st, "mesh_codec_decode_batch_ex")

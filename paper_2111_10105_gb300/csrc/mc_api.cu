@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -1416,8 +1417,8 @@ mesh_codec_status_t mesh_codec_decode_host(mesh_codec_t* h, const uint8_t* bitst
 // ------------------------------------------------------------ batches
 // Grouped CG of a batch (mesh_codec_decode_batch): the FP32 solves whose
 // column count is a multiple of 4 advance together, each phase of an
-// iteration one launch of a persistent grid over a work table of
-// (solve, row block, column tile) items and (solve, column) items; the
+// iteration one launch over a work table of (solve, row block, column tile)
+// items and (solve, column) items, one CTA per item; the
 // table lives in device memory, so one captured graph of 32 iterations
 // serves the whole decode while finished solves leave the table between
 // runs.  Every solve keeps its own geometry, vectors and reduction order,
@@ -1536,9 +1537,9 @@ static mesh_codec_status_t grouped_setup(GroupedCg& G) {
   }
   MC_TRY(cudaMemcpyAsync(G.d_seqs, G.h_seqs, sizeof(CgSeq) * S, cudaMemcpyHostToDevice, G.s));
   MC_TRY(G.upload_tables());
-  // persistent grids: 16 CTAs of 64 threads (row items) / 8 of 256 (columns) per SM
-  G.grid_rows = (int)std::max<size_t>(1, std::min<size_t>(max_items, 152 * 16));
-  G.grid_cols = (int)std::max<size_t>(1, std::min<size_t>(max_cols, 152 * 8));
+  // one CTA per item of the full table (CTAs past the shrinking table return)
+  G.grid_rows = (int)std::max<size_t>(1, max_items);
+  G.grid_cols = (int)std::max<size_t>(1, max_cols);
   // one graph: 32 iterations, then every solve's active-column count to pinned memory
   cudaStream_t cap = G.hs[0]->cap;
   if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MC_E_CUDA;
@@ -1653,7 +1654,7 @@ mesh_codec_status_t mesh_codec_decode_batch_ex(mesh_codec_t* const* handles, int
                                                void* stream) {
   if (!batch_args_ok(handles, count) || !bitstreams || !bytes || !positions_out)
     return MC_E_INVALID_ARG;
-  if (flags & ~MC_BATCH_OWN_STREAMS) return MC_E_INVALID_ARG;
+  if (flags & ~MC_BATCH_GROUPED) return MC_E_INVALID_ARG;
   cudaStream_t s0 = (cudaStream_t)stream;
   MC_TRY(cudaEventRecord(handles[0]->ev_fork, s0));
   std::vector<mesh_codec_status_t> st(count, MC_OK);
@@ -1705,26 +1706,43 @@ mesh_codec_status_t mesh_codec_decode_batch_ex(mesh_codec_t* const* handles, int
     }
     active.push_back(i);
   }
-  // FP32 solves with a multiple of 4 columns advance as one grouped batch;
-  // the others (FP64, frames solves of 3F % 4 != 0 columns, kernel timing)
-  // run their own chunks on their own streams alongside
-  GroupedCg grouped;
+  // with MC_BATCH_GROUPED the FP32 solves with a multiple of 4 columns advance
+  // as grouped batches; the others (FP64, frames solves of 3F % 4 != 0
+  // columns, kernel timing) run their own chunks on their own streams alongside
+  // The candidates are dealt, largest first, over up to kGroups grouped
+  // batches on streams of their own, so that different phases of different
+  // batches (latency-bound gathers, bandwidth-bound updates) overlap.
+  constexpr int kGroups = 4;
+  std::vector<mesh_codec*> cand;
   std::vector<int> alone;
   for (int i : active) {
     mesh_codec* h = handles[i];
     if (h->dec.single && !h->dec.refine && h->dec.Wc % 4 == 0 && h->prof_every == 0)
-      grouped.hs.push_back(h);
+      cand.push_back(h);
     else
       alone.push_back(i);
   }
-  if (grouped.hs.size() < 2 || (flags & MC_BATCH_OWN_STREAMS)) {
+  std::vector<std::unique_ptr<GroupedCg>> groups;
+  if (cand.size() < 2 || !(flags & MC_BATCH_GROUPED)) {
     alone = active;
-    grouped.hs.clear();
   } else {
-    const mesh_codec_status_t gs = grouped_setup(grouped);
-    if (gs != MC_OK) return gs;
+    std::stable_sort(cand.begin(), cand.end(), [](const mesh_codec* a, const mesh_codec* b) {
+      return (long long)a->n * a->dec.Wc > (long long)b->n * b->dec.Wc;
+    });
+    const int ng = std::max(1, std::min<int>(kGroups, (int)cand.size() / 2));
+    for (int g = 0; g < ng; ++g) groups.emplace_back(new GroupedCg());
+    for (size_t q = 0; q < cand.size(); ++q) groups[q % ng]->hs.push_back(cand[q]);
+    for (auto& G : groups) {
+      const mesh_codec_status_t gs = grouped_setup(*G);
+      if (gs != MC_OK) return gs;
+    }
   }
-  while (!alone.empty() || grouped.any_live()) {
+  auto any_group_live = [&]() {
+    for (auto& G : groups)
+      if (G->any_live()) return true;
+    return false;
+  };
+  while (!alone.empty() || any_group_live()) {
     std::vector<int> issued;
     for (int i : alone) {
       mesh_codec* h = handles[i];
@@ -1734,10 +1752,12 @@ mesh_codec_status_t mesh_codec_decode_batch_ex(mesh_codec_t* const* handles, int
         issued.push_back(i);
       }
     }
-    const bool group_ran = grouped.any_live();
-    if (group_ran) {
-      const mesh_codec_status_t gs = grouped_run(grouped);
+    std::vector<GroupedCg*> ran;
+    for (auto& G : groups) {
+      if (!G->any_live()) continue;
+      const mesh_codec_status_t gs = grouped_run(*G);
       if (gs != MC_OK) return gs;
+      ran.push_back(G.get());
     }
     std::vector<int> still;
     for (int i : issued) {
@@ -1745,16 +1765,16 @@ mesh_codec_status_t mesh_codec_decode_batch_ex(mesh_codec_t* const* handles, int
       if (*handles[i]->h_active != 0) still.push_back(i);
     }
     alone.swap(still);
-    if (group_ran) {
-      MC_TRY(cudaEventSynchronize(grouped.ev));
-      const mesh_codec_status_t gs = grouped_retire(grouped);
+    for (GroupedCg* G : ran) {
+      MC_TRY(cudaEventSynchronize(G->ev));
+      const mesh_codec_status_t gs = grouped_retire(*G);
       if (gs != MC_OK) return gs;
     }
   }
-  if (!grouped.hs.empty()) {
-    // every grouped handle's stream continues after the grouped solves
-    MC_TRY(cudaEventRecord(grouped.ev, grouped.s));
-    for (mesh_codec* h : grouped.hs) MC_TRY(cudaStreamWaitEvent(h->own, grouped.ev, 0));
+  for (auto& G : groups) {
+    // every grouped handle's stream continues after its grouped solves
+    MC_TRY(cudaEventRecord(G->ev, G->s));
+    for (mesh_codec* h : G->hs) MC_TRY(cudaStreamWaitEvent(h->own, G->ev, 0));
   }
   for (int i = 0; i < count; ++i) {
     if (st[i] != MC_OK) continue;

@@ -369,27 +369,23 @@ __global__ void k_cg_beta(CgGeom g, const double* __restrict__ partials, double*
 }
 
 // the per-column reductions of a grouped batch (see cg4_grouped_iteration):
-// persistent CTAs over the column items {solve, column}
+// one CTA per column item {solve, column} (CTAs past the table's length return)
 __global__ void k_cgg_alpha(const CgSeq* __restrict__ seqs, const int2* __restrict__ cols,
                             const int* __restrict__ n_cols) {
-  const int nc = *n_cols;
-  for (int it = blockIdx.x; it < nc; it += gridDim.x) {
-    const int2 w = cols[it];
-    const CgSeq& q = seqs[w.x];
-    if (w.y == 0 && threadIdx.x == 0) *q.active = 0;
-    cg_alpha_body(q.g, w.y, q.partials, q.rz, q.alpha, q.done);
-  }
+  if ((int)blockIdx.x >= *n_cols) return;
+  const int2 w = cols[blockIdx.x];
+  const CgSeq& q = seqs[w.x];
+  if (w.y == 0 && threadIdx.x == 0) *q.active = 0;
+  cg_alpha_body(q.g, w.y, q.partials, q.rz, q.alpha, q.done);
 }
 
 __global__ void k_cgg_beta(const CgSeq* __restrict__ seqs, const int2* __restrict__ cols,
                            const int* __restrict__ n_cols) {
-  const int nc = *n_cols;
-  for (int it = blockIdx.x; it < nc; it += gridDim.x) {
-    const int2 w = cols[it];
-    const CgSeq& q = seqs[w.x];
-    cg_beta_body(q.g, w.y, q.partials, q.rz, q.rr, q.bb, q.beta, q.done, q.iters, q.rtol2,
-                 q.max_iters, q.active);
-  }
+  if ((int)blockIdx.x >= *n_cols) return;
+  const int2 w = cols[blockIdx.x];
+  const CgSeq& q = seqs[w.x];
+  cg_beta_body(q.g, w.y, q.partials, q.rz, q.rr, q.bb, q.beta, q.done, q.iters, q.rtol2,
+               q.max_iters, q.active);
 }
 
 void cgg_alpha(const CgSeq* seqs, const int2* cols, const int* n_cols, int grid, cudaStream_t s) {

@@ -417,62 +417,53 @@ __global__ void __launch_bounds__(LANES * kRowLanes) k4_dir(CgGeom g, const floa
 }
 
 // ------------------------------------------------ grouped (work-table) kernels
-// Persistent grids over a table of items: each CTA takes items blockIdx.x,
-// blockIdx.x + gridDim.x, ... and runs the same item body as the per-solve
-// kernels with that solve's geometry and vectors, so every solve of the
-// batch gets the results it gets alone (same row lanes, partials and
-// reduction order).
+// One CTA per item of a table: CTA i runs item i (CTAs past the table's
+// current length return at once; the table only shrinks) with the same item
+// body as the per-solve kernels and that solve's geometry and vectors, so
+// every solve of the batch gets the results it gets alone (same row lanes,
+// partials and reduction order).
 constexpr int kGroupLanes = kGroupCols / 4;
 
 __global__ void __launch_bounds__(kGroupLanes * kRowLanes) k4g_L(const CgSeq* __restrict__ seqs,
                                                                   const int4* __restrict__ items,
                                                                   const int* __restrict__ n_items) {
   extern __shared__ int32_t smem_csr[];
-  const int ni = *n_items;
-  for (int it = blockIdx.x; it < ni; it += gridDim.x) {
-    const int4 w = items[it];
-    const CgSeq& q = seqs[w.x];
-    __syncthreads();   // every thread is done with the previous item's CSR slice
-    k4_L_body<kGroupLanes>(q.g, w.z, w.y, q.row_ptr, q.col_idx, q.deg, q.inv_d, q.kind, q.P, q.T,
-                           q.done, smem_csr);
-  }
+  if ((int)blockIdx.x >= *n_items) return;
+  const int4 w = items[blockIdx.x];
+  const CgSeq& q = seqs[w.x];
+  k4_L_body<kGroupLanes>(q.g, w.z, w.y, q.row_ptr, q.col_idx, q.deg, q.inv_d, q.kind, q.P, q.T,
+                         q.done, smem_csr);
 }
 
 __global__ void __launch_bounds__(kGroupLanes * kRowLanes) k4g_LT(const CgSeq* __restrict__ seqs,
                                                                    const int4* __restrict__ items,
                                                                    const int* __restrict__ n_items) {
   __shared__ double sh[kRowLanes][4 * kGroupLanes + 1];
-  const int ni = *n_items;
-  for (int it = blockIdx.x; it < ni; it += gridDim.x) {
-    const int4 w = items[it];
-    const CgSeq& q = seqs[w.x];
-    k4_LT_body<kGroupLanes>(q.g, w.z, w.y, q.row_ptr, q.col_idx, q.deg, q.inv_d, q.kind,
-                            q.is_anchor, q.T, q.P, q.Q, q.done, q.partials, sh);
-  }
+  if ((int)blockIdx.x >= *n_items) return;
+  const int4 w = items[blockIdx.x];
+  const CgSeq& q = seqs[w.x];
+  k4_LT_body<kGroupLanes>(q.g, w.z, w.y, q.row_ptr, q.col_idx, q.deg, q.inv_d, q.kind,
+                          q.is_anchor, q.T, q.P, q.Q, q.done, q.partials, sh);
 }
 
 __global__ void __launch_bounds__(kGroupLanes * kRowLanes, 1024 / (kGroupLanes * kRowLanes))
     k4g_update(const CgSeq* __restrict__ seqs, const int4* __restrict__ items,
                const int* __restrict__ n_items) {
   __shared__ double sh[kRowLanes][4 * kGroupLanes + 1];
-  const int ni = *n_items;
-  for (int it = blockIdx.x; it < ni; it += gridDim.x) {
-    const int4 w = items[it];
-    const CgSeq& q = seqs[w.x];
-    k4_update_body<kGroupLanes>(q.g, w.z, w.y, q.X, q.R, q.P, q.Q, q.inv_diag, q.alpha, q.done,
-                                q.partials, sh);
-  }
+  if ((int)blockIdx.x >= *n_items) return;
+  const int4 w = items[blockIdx.x];
+  const CgSeq& q = seqs[w.x];
+  k4_update_body<kGroupLanes>(q.g, w.z, w.y, q.X, q.R, q.P, q.Q, q.inv_diag, q.alpha, q.done,
+                              q.partials, sh);
 }
 
 __global__ void __launch_bounds__(kGroupLanes * kRowLanes) k4g_dir(const CgSeq* __restrict__ seqs,
                                                                     const int4* __restrict__ items,
                                                                     const int* __restrict__ n_items) {
-  const int ni = *n_items;
-  for (int it = blockIdx.x; it < ni; it += gridDim.x) {
-    const int4 w = items[it];
-    const CgSeq& q = seqs[w.x];
-    k4_dir_body<kGroupLanes>(q.g, w.z, w.y, q.R, q.P, q.inv_diag, q.beta, q.done);
-  }
+  if ((int)blockIdx.x >= *n_items) return;
+  const int4 w = items[blockIdx.x];
+  const CgSeq& q = seqs[w.x];
+  k4_dir_body<kGroupLanes>(q.g, w.z, w.y, q.R, q.P, q.inv_diag, q.beta, q.done);
 }
 
 }  // namespace

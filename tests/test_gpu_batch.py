@@ -82,9 +82,10 @@ def test_batch_mixed_autotuned_against_oracle():
           for spec, (tris, pos) in zip(MIXED, seqs)]
     pos_d = [torch.from_numpy(p).cuda() for _, p in seqs]
     bits = encode_batch(cs, pos_d)
-    # two decodes: the automatic solve mode keeps the anchor response on the second
-    for _ in range(2):
-        recs = decode_batch(cs, bits)
+    # two decodes: the automatic solve mode keeps the anchor response on the
+    # second; the first with each sequence on its own stream, the second grouped
+    for rnd in range(2):
+        recs = decode_batch(cs, bits, grouped=rnd == 1)
         for spec, (tris, pos), r in zip(MIXED, seqs, recs):
             p = oc.Params(n_frames=spec.n_frames, rank=spec.rank, n_anchors=spec.n_anchors,
                           seed=spec.seed, oi_sweeps=25)
@@ -96,7 +97,7 @@ def test_batch_mixed_autotuned_against_oracle():
 
 
 def test_grouped_batch_equals_single_decodes():
-    # the FP32 solves of a batch advance as one grouped batch (work-table
+    # the FP32 solves of a batch advance as grouped batches (work-table
     # kernels over all sequences); every sequence's reconstruction must equal,
     # to the bit, the one its own handle gives alone, on the first decode
     # (frames or factored solves) and on the second (kept anchor response)
@@ -114,7 +115,7 @@ def test_grouped_batch_equals_single_decodes():
     pos_d = [torch.from_numpy(p).cuda() for _, p in seqs]
     bits = encode_batch(cs, pos_d)
     for rnd in range(3):
-        recs = decode_batch(cs, bits)
+        recs = decode_batch(cs, bits, grouped=True)
         for c, b, r in zip(singles, bits, recs):
             r1 = c.decode(b)
             assert torch.equal(r1, r), rnd
