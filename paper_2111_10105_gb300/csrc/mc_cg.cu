@@ -43,8 +43,11 @@ CgGeom cg_geometry_rows(int n, int W, int rpb) {
 // width plus the adjacency's bandwidth, times the row length) then stay in
 // L2, where long row blocks spread the resident CTAs over the whole matrix
 // and evict them (measured on the 99,856-vertex grid with 1,192 FP32
-// columns: 3x the algorithmic DRAM reads with 1,561-row blocks).
-static constexpr int kMaxRows = 64;
+// columns: 3x the algorithmic DRAM reads with 1,561-row blocks).  Measured
+// per FP32 iteration with 192 columns: 32 rows 0.286 ms, 64 rows 0.241 ms,
+// 128 rows 0.229 ms, 256 rows 0.253 ms (99,856-vertex grid); 128 rows 0.605
+// ms against 0.640 ms at 256 on the 262,144-vertex grid.
+static constexpr int kMaxRows = 128;
 
 CgGeom cg_geometry(int n, int W) {
   int col_tiles = (W + 31) / 32;
