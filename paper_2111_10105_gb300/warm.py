@@ -89,10 +89,11 @@ class WarmStart:
             raise ValueError(start)
         return _c.warm_compose(x_last, self.F, pred), delta, anc
 
-    def observe_decoded(self, x, delta, anc):
-        """Learn from a decoded segment (the pair previous -> this one), then
-        make it the previous segment."""
-        if self.x_prev is not None:
+    def observe_decoded(self, x, delta, anc, fit=True):
+        """Learn from a decoded segment (the pair previous -> this one; not with
+        fit=False, e.g. once the network is trained), then make it the
+        previous segment."""
+        if fit and self.x_prev is not None:
             feat, tgt = _c.warm_features(self.x_prev[-1], anc, self.anchors, self.nearest,
                                          self.dist, delta, self.delta_prev, x_cur=x)
             self.pos.fit(feat, tgt)
@@ -118,9 +119,10 @@ class WarmStart:
             raise ValueError(start)
         return _c.basis_compose(self.U_prev, pred)
 
-    def observe_basis(self, U):
-        """Learn from an encoded segment's dictionary, then keep it."""
-        if self.U_prev is not None:
+    def observe_basis(self, U, fit=True):
+        """Learn from an encoded segment's dictionary (not with fit=False),
+        then keep it."""
+        if fit and self.U_prev is not None:
             feat, tgt = _c.basis_features(self.U_prev, U)
             self.basis.fit(feat, tgt)
         self.U_prev = U.clone()
