@@ -600,25 +600,28 @@ def run_profile_case(args):
               coeff_bits=spec.coeff_bits, dict_bits=spec.dict_bits,
               anchor_bits=spec.anchor_bits, oi_sweeps=SWEEPS, precision=prec,
               oi_refine_sweeps=1 if prec else 0, cg_rtol=cg_rtol, refine=args.refine,
-              solve_mode={"frames": 0, "factored": 1}[args.solve_mode])
+              solve_mode={"frames": 0, "factored": 1}[args.solve_mode], block_cg=args.block_cg)
     if args.cg_max_iters:
         kw["cg_max_iters"] = args.cg_max_iters
     pos_dev = torch.from_numpy(pos).cuda()
-    counts, iters = [], []
+    counts, iters, secs = [], [], []
     with MeshCodec(tris, n, **kw) as mc:
         counts.append(("create", mc.stats()["launches_create"]))
         for phase in ("cold", "warm"):
             bits = mc.encode(pos_dev)
             torch.cuda.synchronize()
             counts.append((phase + "_encode", mc.stats()["launches_encode"]))
+            t0 = time.perf_counter()
             mc.decode(bits, allow_not_converged=True)
             torch.cuda.synchronize()
+            secs.append((phase, round(time.perf_counter() - t0, 4)))
             st = mc.stats()
             counts.append((phase + "_decode", st["launches_decode"]))
             iters.append((phase, st["cg_iterations_run"]))
     print(json.dumps({"profile_case": args.workload, "precision": args.precision,
-                      "refine": args.refine, "cg_columns": st["cg_columns"],
-                      "cg_iterations_run": dict(iters),
+                      "refine": args.refine, "block_cg": args.block_cg,
+                      "cg_columns": st["cg_columns"],
+                      "cg_iterations_run": dict(iters), "decode_s": dict(secs),
                       "launches": counts,
                       "launches_before_warm_decode": sum(c for _, c in counts[:-1])}),
           flush=True)
@@ -1228,6 +1231,9 @@ def main(argv=None):
                          "decode of the workload, launch counts printed (not a benchmark)")
     ap.add_argument("--cg-max-iters", type=int, default=0,
                     help="--profile-case: CG iteration cap (0: the codec's default)")
+    ap.add_argument("--block-cg", type=int, choices=[0, 1], default=0,
+                    help="--profile-case with --refine: block CG (groups of 64 columns) as the "
+                         "refined solve's inner solver instead of one CG per column")
     ap.add_argument("--solve-mode", choices=["frames", "factored"], default="factored",
                     help="decoder right-hand sides: 3F frame columns (Eq. 11-12 as written) or "
                          "3k + n_c factored columns (same solution, reassociated)")
@@ -1240,6 +1246,8 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.block_cg and not (args.profile_case and args.refine):
+        ap.error("--block-cg needs --profile-case and a refined solve (--refine > 0)")
     if args.profile_case:
         return run_profile_case(args)
     if args.workload == "batched64":

@@ -140,7 +140,15 @@ typedef struct mesh_codec_params {
                                     refinement sweeps and Rayleigh-Ritz correct */
     int32_t layout;              /* mesh_codec_layout_t of every positions argument; the
                                     blocks variant needs MC_LAYOUT_FRAMES */
-    int32_t reserved[1];         /* must be zero */
+    int32_t block_cg;            /* refined solve's inner solver (refine > 0 only):
+                                    0 = one preconditioned CG per column; 1 = block CG
+                                    (O'Leary): the columns in groups of 64 share one Krylov
+                                    space, directions orthonormalised by CholeskyQR twice
+                                    (FP32 vectors, FP64-summed Gram matrices, FP64 64 x 64
+                                    algebra); the outer FP64 residual test is the same.
+                                    The factored solves pad their columns to a multiple
+                                    of 4 for it; a frames solve with 3F not a multiple of
+                                    4 keeps the column CG */
 } mesh_codec_params_t;
 
 typedef struct mesh_codec_stats {

@@ -48,7 +48,7 @@ class Params(ctypes.Structure):
         ("oi_refine_sweeps", ctypes.c_int32), ("autotune", ctypes.c_int32),
         ("block_delta", ctypes.c_int32), ("block_delta_bits", ctypes.c_int32),
         ("refine", ctypes.c_int32), ("layout", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 1),
+        ("block_cg", ctypes.c_int32),
     ]
 
 

@@ -197,7 +197,8 @@ bool valid_params(const mesh_codec_params_t* p) {
   if (p->block_delta_bits < 0 || p->block_delta_bits > MESH_CODEC_MAX_BITS) return false;
   if (p->refine < 0 || p->refine > 12) return false;
   if (p->layout != MC_LAYOUT_FRAMES && p->layout != MC_LAYOUT_VERTEX_MAJOR) return false;
-  if (p->reserved[0] != 0) return false;
+  if (p->block_cg != 0 && p->block_cg != 1) return false;
+  if (p->block_cg && p->refine == 0) return false;
   return true;
 }
 
@@ -245,6 +246,7 @@ void mesh_codec_destroy(mesh_codec_t* h) {
   cudaDeviceSynchronize();
   if (h->ws) cudaFree(h->ws);
   if (h->Gcache) cudaFree(h->Gcache);
+  mc::bcg_release(h);
   if (h->Gcache_anchors) cudaFree(h->Gcache_anchors);
   if (h->Glp) cudaFree(h->Glp);
   if (h->Ahlp) cudaFree(h->Ahlp);
@@ -741,10 +743,10 @@ static void decode_prepare(mesh_codec* h, const uint8_t* in, cudaStream_t s, Lau
   }
   // CG columns: 3F frames (Eq. 11-12 as written), or 3k + n_c factored columns,
   // or the 3k data columns with the kept anchor response (the FP32 factored
-  // solve pads its column count to a multiple of 4 with zero right-hand
-  // sides, which converge at once, for the float4 kernels)
+  // solve and the block CG pad the column count to a multiple of 4 with zero
+  // right-hand sides, which converge at once, for the float4 kernels)
   d.Wc = d.factored ? (d.cached ? 3 * k : 3 * k + h->n_c) : W;
-  if (d.factored && h->lp >= 0) d.Wc = (d.Wc + 3) / 4 * 4;
+  if (d.factored && (h->lp >= 0 || h->p.block_cg)) d.Wc = (d.Wc + 3) / 4 * 4;
   if (!d.factored) {
     // delta~_c = (U_c' C_c')^T : (n x k)(k x F) into D[:, cF : cF + F]
     if (h->lp >= 0 && h->p.refine == 0) {
@@ -945,6 +947,15 @@ static mesh_codec_status_t decode_refine(mesh_codec* h, cudaStream_t s, Launches
     // 1000): a column whose FP32 correction cannot reach the inner tolerance
     // moves on to the next outer step instead of spinning
     const int inner_max = std::max(1000, h->p.cg_max_iters / 8);
+    if (h->p.block_cg && W % 4 == 0) {
+      const int ran = bcg_solve(h, d.geom, (const float*)d.inv_d, (const float*)d.inv_diag, Rres,
+                                X32, R32, P32, T32, Q32, h->cg.iters, inner_rtol, inner_max, s,
+                                L);
+      if (ran < 0) return MC_E_CUDA;
+      d.it += ran;
+      refine_update(X32, nw, X64, h->cg.iters, W, h->ref_iters, s, L);
+      continue;
+    }
     cg_init(d.geom, Rres, X32, R32, P32, d.inv_diag, h->cg, 1, s, L);
     for (int it = 0; it < inner_max; it += kCgChunk) {
       const int m = std::min(kCgChunk, inner_max - it);

@@ -6,6 +6,10 @@
 
 #include "mc_internal.cuh"
 
+namespace mc {
+struct BcgWs;   // block CG workspace (mc_bcg.cu)
+}
+
 // per-decode state carried between the decoder's phases
 struct DecodeState {
   bool factored = false;
@@ -62,6 +66,9 @@ struct mesh_codec {
   // refined solve: per column ||B||^2, ||R||^2, converged flag, iterations
   double *ref_bb, *ref_rr, *ref_prev;
   int32_t *ref_frozen, *ref_iters;
+  // block CG of the refined solve (own allocation, made on first use)
+  mc::BcgWs* bcg = nullptr;
+  void* bcg_mem = nullptr;
   mc::CgState cg;
   uint32_t* d_status;
   int nnz;
@@ -133,4 +140,12 @@ void mixed_project(mesh_codec* h, cudaStream_t s, Launches& L);
 void mixed_backproject(mesh_codec* h, cudaStream_t s, Launches& L);
 bool mixed_finish(mesh_codec* h, const double* Y, long long y_ld, const double* G, long long g_ld,
                   const double* A, bool data_product, cudaStream_t s, Launches& L);
+// Block CG (mc_bcg.cu): M D = R0 (R0 FP64 [n][W]) for every column to
+// ||r|| <= tol ||r_0||, over groups of 64 columns; D into X32 (FP32), the
+// iterations of each column's group into iters.  R32, P32, T32, Q32 are FP32
+// [n][W] scratch.  Returns the iterations run, or -1 on a CUDA error.
+int bcg_solve(mesh_codec* h, const CgGeom& geom, const float* inv_d, const float* inv_diag,
+              const double* R0, float* X32, float* R32, float* P32, float* T32, float* Q32,
+              int32_t* iters, double tol, int max_iters, cudaStream_t s, Launches& L);
+void bcg_release(mesh_codec* h);
 }  // namespace mc

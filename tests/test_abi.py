@@ -91,9 +91,12 @@ def test_invalid_params_rejected_before_any_device_work(lib):
         assert lib.mesh_codec_create(ctypes.byref(p), ctypes.cast(tris, ctypes.c_void_p), 0, None,
                                      0, None, ctypes.byref(h)) == 1
         setattr(p, field, 0)
-    p.reserved[0] = 1
-    assert lib.mesh_codec_create(ctypes.byref(p), ctypes.cast(tris, ctypes.c_void_p), 0, None, 0,
-                                 None, ctypes.byref(h)) == 1
+    # block CG only as the refined solve's inner solver, and only 0 / 1
+    for refine, block in ((0, 1), (2, 2), (2, -1)):
+        p.refine, p.block_cg = refine, block
+        assert lib.mesh_codec_create(ctypes.byref(p), ctypes.cast(tris, ctypes.c_void_p), 0, None,
+                                     0, None, ctypes.byref(h)) == 1
+    p.refine, p.block_cg = 0, 0
     assert lib.mesh_codec_create(None, None, 0, None, 0, None, ctypes.byref(h)) == 1
     lib.mesh_codec_destroy(None)
 

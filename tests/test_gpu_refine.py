@@ -92,3 +92,63 @@ def test_refined_mixed_precision_reaches_fp64_quality():
     # TF32 dictionary differs (measured 2.4% above)
     assert abs(nm["tf32_refined"] - nm["fp64"]) <= 0.05 * nm["fp64"]
     assert abs(nm["tf32_refined"] - nm["fp64"]) < abs(nm["tf32"] - nm["fp64"])
+
+
+@pytest.mark.parametrize("mode,n_anchors", [(0, 20), (1, 20), (1, 21)],
+                         ids=["frames", "factored", "factored_padded"])
+def test_block_cg_refined_solve_matches_the_oracle(mode, n_anchors):
+    # block CG (groups of 64 columns) as the inner solver: frames 3F = 144
+    # columns (groups 64 + 64 + 16), factored 3k + n_c = 44 columns, and 45
+    # padded to 48 with a zero right-hand side
+    spec = SequenceSpec(name="b", mesh="icosphere:4", n_frames=48, rank=8,
+                        n_anchors=n_anchors, seed=41)
+    tris, pos = make_sequence(spec)
+    n = pos.shape[1]
+    o = oc.encode(tris, pos, oc.Params(n_frames=spec.n_frames, rank=spec.rank,
+                                       n_anchors=spec.n_anchors, seed=spec.seed))
+    e_o = metrics.nmse(pos, oc.decode(o, tris))
+    ot = torch.from_numpy(np.frombuffer(o, dtype=np.uint8).copy()).cuda()
+    with _codec(tris, n, spec, solve_mode=mode, refine=3, block_cg=1) as mc:
+        rec = mc.decode(ot).cpu().numpy()
+        st = mc.stats()
+        # (a factored decode after the first keeps the anchor response: 3k columns)
+        second = mc.decode(ot).cpu().numpy()
+        third = mc.decode(ot).cpu().numpy()
+    with _codec(tris, n, spec, solve_mode=mode, refine=3) as mc:
+        col = mc.decode(ot).cpu().numpy()
+        st_col = mc.stats()
+    want = 3 * spec.n_frames if mode == 0 else (3 * spec.rank + n_anchors + 3) // 4 * 4
+    assert st["cg_columns"] == want
+    print("inner iterations: block", st["cg_iterations_run"], "column", st_col["cg_iterations_run"])
+    assert st["cg_not_converged"] == 0
+    assert st["cg_rel_residual_max"] <= 1e-11
+    assert abs(metrics.nmse(pos, rec) - e_o) <= NMSE_RTOL * e_o
+    # fixed-order reductions: the same solve repeated is bit-identical
+    np.testing.assert_array_equal(third, second)
+    scale = np.abs(col).max()
+    for x in (rec, second):
+        assert np.abs(x - col).max() <= 1e-10 * scale
+
+
+def test_block_cg_mixed_precision_and_batch():
+    # TF32 dictionary sweeps with the refined block-CG solve: within 1% of the
+    # FP64 decode's NMSE on the near-lossless torus; the batch entry point
+    # runs the same solve
+    from paper_2111_10105_gb300.codec import decode_batch
+    spec = SequenceSpec(name="t", mesh="torus:60:30", n_frames=48, rank=40, n_anchors=18,
+                        seed=80, bend=0.1)
+    tris, pos = make_sequence(spec)
+    n = pos.shape[1]
+    pos_d = torch.from_numpy(pos).cuda()
+    p = oc.Params(n_frames=spec.n_frames, rank=spec.rank, n_anchors=spec.n_anchors,
+                  seed=spec.seed, oi_sweeps=30)
+    e_o = metrics.nmse(pos, oc.decode(oc.encode(tris, pos, p), tris))
+    with _codec(tris, n, spec, precision=1, oi_refine_sweeps=1, oi_sweeps=30, refine=2,
+                block_cg=1, cg_rtol=1e-13) as mc:
+        bits = mc.encode(pos_d).clone()
+        rec = mc.decode(bits).cpu().numpy()
+        out = torch.empty_like(pos_d)
+        decode_batch([mc], [bits], outs=[out])
+        batched = out.cpu().numpy()
+    assert abs(metrics.nmse(pos, rec) - e_o) <= 0.01 * e_o
+    np.testing.assert_array_equal(batched, rec)
