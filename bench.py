@@ -46,16 +46,19 @@ DEFAULT_WORKLOAD = "grid512_F300_k64"
 # oracle (on the noise-free 512 x 512 grid the plain TF32 path misses the 1%
 # bound; TF32 sweeps with the refined solve meet it)
 WORKLOAD_DEFAULTS = {
-    "grid512_F300_k64": {"precision": "tf32", "refine": 2, "anchors": "random"},
+    "grid512_F300_k64": {"precision": "tf32", "refine": 5, "anchors": "random"},
     "grid316_F512_k64": {"precision": "tf32", "refine": 0, "anchors": "random"},
     "grid256_F256_k64": {"precision": "tf32", "refine": 2, "anchors": "random"},
 }
 FORM_DEFAULT = {"precision": "fp64", "refine": 0, "anchors": "farthest"}
 # the refined solve's FP64 residual tolerance per workload (else 1e-14): on
-# the 512 x 512 grid a residual of 1e-9 gives the oracle's NMSE to 9e-5
-# relative (bound 1e-2) in 4,608 FP32 iterations a decode; 1e-11 gives 4e-6
-# in 5,824 and 1e-14 3e-7 in 19,284 (the last decades sit at the binary64
-# floor)
+# the 512 x 512 grid a residual of 1e-9 gives the oracle's NMSE to 3e-4
+# relative (bound 1e-2) in 3,520 FP32 iterations a decode with corrections of
+# up to 5 decades (each column's last correction stops at what the 1e-9 test
+# still needs; 2 / 3 / 4 / 6 / 7 decades took 4,320 / 4,000 / 3,744 / 3,584 /
+# 3,552); a residual of 1e-11 gave 4e-6 and 1e-14 3e-7 at a higher count
+# (the last decades sit at the binary64 floor).  The 256 x 256 profiling case
+# keeps 2 decades, the form its profiles were taken in.
 REFINED_RTOL = {"grid512_F300_k64": 1e-9, "grid256_F256_k64": 1e-9}
 SWEEPS = 30
 # stated NMSE bounds relative to the FP64 oracle's NMSE, per precision mode
@@ -88,7 +91,9 @@ MEASURED_TRAFFIC = {
     # rules allow: its k4_update traffic is the 256x256 capture's 23.7 DRAM
     # bytes per vertex-column entry (1,314 MB over 65,536 x 848 entries, the
     # algorithmic 24 B) scaled to 262,144 x 192 entries
-    ("grid512_F300_k64", "tf32", 2, 192, "k_cg_update"):
+    # (workload, precision, refined solve, CG columns, kernel): the FP32 CG
+    # kernels are the same for any number of correction decades
+    ("grid512_F300_k64", "tf32", True, 192, "k_cg_update"):
         (23.67 * 262144 * 192, "profiles/k4_update_L_LT_grid256_F256_k64_tf32.md, "
                                "per-entry bytes scaled to the 512x512 launch"),
 }
@@ -509,7 +514,7 @@ def run_ours(args):
     nnz = int(mc.buffer(1).numel())
     cols = stats["cg_columns"]
     rl = roofline(profile, stats, n, cols, nnz, spec.n_anchors, peaks, single)
-    measured = MEASURED_TRAFFIC.get((args.workload, args.precision, args.refine, cols,
+    measured = MEASURED_TRAFFIC.get((args.workload, args.precision, args.refine > 0, cols,
                                      rl["kernel"]))
     if measured:
         active = stats["cg_iters_mean"] / max(1, stats["cg_iters_max"])

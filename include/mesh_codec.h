@@ -131,8 +131,10 @@ typedef struct mesh_codec_params {
     int32_t refine;              /* decoder solve: 0 = CG in the precision of the mode;
                                     r in 1..12 = iterative refinement: the residual of Eq. 12's
                                     normal equations in FP64, FP32 CG corrections solved to a
-                                    relative 10^-r, until every column's FP64 residual meets
-                                    cg_rtol (FP64 accuracy from FP32 sweeps, any precision).
+                                    relative 10^-r (a column whose residual needs less to meet
+                                    cg_rtol stops at that, with a factor-2 margin), until every
+                                    column's FP64 residual meets cg_rtol (FP64 accuracy from
+                                    FP32 sweeps, any precision).
                                     In the TF32 / BF16 modes refine > 0 also keeps the
                                     projection (Eq. 9), the back-projection (Eq. 11) and the
                                     decoder's final products in FP64: the tensor cores then

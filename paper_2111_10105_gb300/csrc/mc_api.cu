@@ -112,6 +112,7 @@ size_t carve(mesh_codec* h, void* base) {
   h->ref_bb = c.take<double>(W);
   h->ref_rr = c.take<double>(W);
   h->ref_prev = c.take<double>(W);
+  h->ref_t2 = c.take<double>(W);
   h->ref_frozen = c.take<int32_t>(W);
   h->ref_iters = c.take<int32_t>(W);
   size_t off = mixed_carve(h, (char*)base, c.off);
@@ -948,15 +949,19 @@ static mesh_codec_status_t decode_refine(mesh_codec* h, cudaStream_t s, Launches
     // moves on to the next outer step instead of spinning
     const int inner_max = std::max(1000, h->p.cg_max_iters / 8);
     if (h->p.block_cg && W % 4 == 0) {
+      refine_targets(h->ref_rr, h->ref_bb, h->ref_frozen, W, h->p.cg_rtol, inner_rtol,
+                     h->ref_t2, nullptr, s, L);
       const int ran = bcg_solve(h, d.geom, (const float*)d.inv_d, (const float*)d.inv_diag, Rres,
-                                X32, R32, P32, T32, Q32, h->cg.iters, inner_rtol, inner_max, s,
-                                L);
+                                X32, R32, P32, T32, Q32, h->cg.iters, inner_rtol, h->ref_t2,
+                                inner_max, s, L);
       if (ran < 0) return MC_E_CUDA;
       d.it += ran;
       refine_update(X32, nw, X64, h->cg.iters, W, h->ref_iters, s, L);
       continue;
     }
     cg_init(d.geom, Rres, X32, R32, P32, d.inv_diag, h->cg, 1, s, L);
+    refine_targets(h->ref_rr, h->ref_bb, h->ref_frozen, W, h->p.cg_rtol, inner_rtol, h->ref_t2,
+                   h->cg.bb, s, L);
     for (int it = 0; it < inner_max; it += kCgChunk) {
       const int m = std::min(kCgChunk, inner_max - it);
       // timing: the first m - 1 iterations as one run, the last one per kernel

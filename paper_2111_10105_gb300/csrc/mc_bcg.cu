@@ -11,7 +11,8 @@
 //   X += P alpha,  R -= Q alpha
 //   K = (D^-1 Q)^T R,  beta = -G^-1 K      (D = diag M, the Jacobi preconditioner)
 //   P = orth(D^-1 R + P beta)              (CholeskyQR, twice)
-// A group stops when each of its columns has ||r|| <= tol ||r_0||.
+// A group stops when each of its columns has ||r|| <= tol ||r_0|| (scaled per
+// column by the refined solve's inner target).
 //
 // Precision.  The vectors are FP32.  The Gram matrices take FP32 products
 // summed in FP32 over the rows one thread visits in a chunk of kChunkRows
@@ -322,14 +323,15 @@ __global__ void __launch_bounds__(256) k_bapply(const Factor* __restrict__ F_all
   out_all[(long long)g * kS * kS + i * kS + col] = (float)(sign * f.dsc[i] * s);
 }
 
-// a group is done when every column has ||r||^2 <= tol^2 ||r_0||^2 (columns
+// a group is done when every column has ||r||^2 <= tol^2 t2 ||r_0||^2 (columns
 // past W count as converged); the iteration that ends a group is counted and
 // *active counts the groups still open
-__global__ void k_bconverge(const double* __restrict__ rr, const double* __restrict__ rr0, int W,
-                            double tol2, int32_t* gdone, int32_t* git, int32_t* active) {
+__global__ void k_bconverge(const double* __restrict__ rr, const double* __restrict__ rr0,
+                            const double* __restrict__ t2, int W, double tol2, int32_t* gdone,
+                            int32_t* git, int32_t* active) {
   const int g = blockIdx.x, c = threadIdx.x, col = g * kS + c;
   if (gdone[g]) return;
-  const bool conv = col >= W || rr[col] <= tol2 * rr0[col];
+  const bool conv = col >= W || rr[col] <= tol2 * rr0[col] * (t2 ? t2[col] : 1.0);
   const bool all = __syncthreads_and(conv);
   if (c == 0) {
     git[g] += 1;
@@ -558,7 +560,8 @@ void bcg_release(mesh_codec* h) {
 
 int bcg_solve(mesh_codec* h, const CgGeom& geom, const float* inv_d, const float* inv_diag,
               const double* R0, float* X32, float* R32, float* P32, float* T32, float* Q32,
-              int32_t* iters, double tol, int max_iters, cudaStream_t s, Launches& L) {
+              int32_t* iters, double tol, const double* t2, int max_iters, cudaStream_t s,
+              Launches& L) {
   const int n = h->n, W = geom.W;
   if (!bcg_attributes()) return -1;
   if (!h->bcg || h->bcg->W != W || h->bcg->n != n) {
@@ -616,7 +619,8 @@ int bcg_solve(mesh_codec* h, const CgGeom& geom, const float* inv_d, const float
       k_breduce<<<grid1(gm), 256, 0, s>>>(b.part, b.Hm, nullptr, nullptr, b.chunks, gm);
       k_breduce<<<grid1(W), 256, 0, s>>>(b.sq_part, b.rr, nullptr, nullptr, b.chunks, W);
       k_bapply<<<gapply, 256, 0, s>>>(b.fac, b.Hm, -1.0, b.gdone, b.beta);
-      k_bconverge<<<b.ngroups, kS, 0, s>>>(b.rr, b.rr0, W, tol2, b.gdone, b.git, b.active);
+      k_bconverge<<<b.ngroups, kS, 0, s>>>(b.rr, b.rr0, t2, W, tol2, b.gdone, b.git,
+                                           b.active);
       // P = orth(D^-1 R + P beta)
       bmul<2>(b, P32, b.beta, R32, inv_diag, T32, s);
       L.add(14);

@@ -767,6 +767,24 @@ void refine_residual(const CgGeom& g, const int32_t* row_ptr, const int32_t* col
   L.add(3);
 }
 
+__global__ void k_refine_targets(const double* __restrict__ rr, const double* __restrict__ bb,
+                                 const int32_t* __restrict__ frozen, int W, double rtol,
+                                 double inner, double* __restrict__ t2, double* cg_bb) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < W; c += gridDim.x * blockDim.x) {
+    double t = 0.5;
+    if (!frozen[c] && rr[c] > 0.0) t = fmin(0.5, fmax(inner, 0.5 * rtol * sqrt(bb[c] / rr[c])));
+    const double q = frozen[c] ? 1.0 : (t / inner) * (t / inner);
+    t2[c] = q;
+    if (cg_bb) cg_bb[c] *= q;
+  }
+}
+
+void refine_targets(const double* rr, const double* bb, const int32_t* frozen, int W, double rtol,
+                    double inner_rtol, double* t2, double* cg_bb, cudaStream_t s, Launches& L) {
+  k_refine_targets<<<(W + 255) / 256, 256, 0, s>>>(rr, bb, frozen, W, rtol, inner_rtol, t2, cg_bb);
+  L.add(1);
+}
+
 void refine_update(const float* D, long long count, double* X, const int32_t* iters, int W,
                    int32_t* total, cudaStream_t s, Launches& L) {
   k_refine_add<<<(int)std::min<long long>((count + 255) / 256, 152 * 16), 256, 0, s>>>(D, count,

@@ -65,6 +65,7 @@ struct mesh_codec {
   int32_t* d_match = nullptr;      // device: anchors differing from the kept set
   // refined solve: per column ||B||^2, ||R||^2, converged flag, iterations
   double *ref_bb, *ref_rr, *ref_prev;
+  double* ref_t2;                  // per column (inner target / 10^-refine)^2
   int32_t *ref_frozen, *ref_iters;
   // block CG of the refined solve (own allocation, made on first use)
   mc::BcgWs* bcg = nullptr;
@@ -141,11 +142,12 @@ void mixed_backproject(mesh_codec* h, cudaStream_t s, Launches& L);
 bool mixed_finish(mesh_codec* h, const double* Y, long long y_ld, const double* G, long long g_ld,
                   const double* A, bool data_product, cudaStream_t s, Launches& L);
 // Block CG (mc_bcg.cu): M D = R0 (R0 FP64 [n][W]) for every column to
-// ||r|| <= tol ||r_0||, over groups of 64 columns; D into X32 (FP32), the
+// ||r||^2 <= tol^2 t2[col] ||r_0||^2 (t2 null: 1), over groups of 64 columns; D into X32 (FP32), the
 // iterations of each column's group into iters.  R32, P32, T32, Q32 are FP32
 // [n][W] scratch.  Returns the iterations run, or -1 on a CUDA error.
 int bcg_solve(mesh_codec* h, const CgGeom& geom, const float* inv_d, const float* inv_diag,
               const double* R0, float* X32, float* R32, float* P32, float* T32, float* Q32,
-              int32_t* iters, double tol, int max_iters, cudaStream_t s, Launches& L);
+              int32_t* iters, double tol, const double* t2, int max_iters, cudaStream_t s,
+              Launches& L);
 void bcg_release(mesh_codec* h);
 }  // namespace mc

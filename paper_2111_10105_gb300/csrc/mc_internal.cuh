@@ -234,6 +234,14 @@ void refine_residual(const CgGeom& g, const int32_t* row_ptr, const int32_t* col
                      double* rr, int32_t* active, cudaStream_t s, Launches& L);
 void refine_update(const float* D, long long count, double* X, const int32_t* iters, int W,
                    int32_t* total, cudaStream_t s, Launches& L);
+// Inner target of each column's correction: the relative reduction
+// t = clamp(0.5 rtol ||B|| / ||R||, inner_rtol, 0.5) that brings the FP64
+// residual below rtol ||B|| with a factor-2 margin, so no step solves further
+// than the outer test needs; t2[col] = (t / inner_rtol)^2 (1 for frozen
+// columns), and cg_bb[col] *= t2[col] when cg_bb is set (the CG's stop test
+// rr <= inner_rtol^2 bb then stops at t)
+void refine_targets(const double* rr, const double* bb, const int32_t* frozen, int W, double rtol,
+                    double inner_rtol, double* t2, double* cg_bb, cudaStream_t s, Launches& L);
 // CG start from the X already in place (warm start), T and Q as scratch
 void cg_init_warm(const CgGeom& g, const int32_t* row_ptr, const int32_t* col_idx,
                   const int32_t* deg, const void* inv_d, const uint8_t* is_anchor, int kind,
