@@ -490,19 +490,18 @@ size_t bcg_carve(BcgWs& b, char* base) {
   return off;
 }
 
+// the kernels above 48 KB of dynamic shared memory (set on every solve: the
+// attribute belongs to the current device)
 bool bcg_attributes() {
-  static bool done = false;
-  if (done) return true;
   const int fs = (int)sizeof(FactorSmem), ms = (int)kMulSmem;
   const cudaFuncAttribute attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  done = cudaFuncSetAttribute(k_bfactor<0>, attr, fs) == cudaSuccess &&
+  return cudaFuncSetAttribute(k_bfactor<0>, attr, fs) == cudaSuccess &&
          cudaFuncSetAttribute(k_bfactor<1>, attr, fs) == cudaSuccess &&
          cudaFuncSetAttribute(k_bmul<0>, attr, ms) == cudaSuccess &&
          cudaFuncSetAttribute(k_bmul<1>, attr, ms) == cudaSuccess &&
          cudaFuncSetAttribute(k_bmul<2>, attr, ms) == cudaSuccess &&
          cudaFuncSetAttribute(k_bmul<3>, attr, ms) == cudaSuccess &&
          cudaFuncSetAttribute(k_bmul<4>, attr, ms) == cudaSuccess;
-  return done;
 }
 
 GramArgs gram_args(const BcgWs& b, GramPair p0, GramPair p1, const float* scale_a,
