@@ -502,11 +502,19 @@ def run_ours(args):
     mc.decode_host(bits_h, out=rec_h, stream=stream)
     if dist is not None:
         dist.barrier()
+    e2e_sampler = ClockSampler(uuid)
+    e2e_sampler.start()
     t0 = time.perf_counter()
+    e2e_step_s, e2e_iters = [], []
     for _ in range(e2e_steps):
+        ts = time.perf_counter()
         mc.encode_host(pos_h, out=bits_h, stream=stream)
+        tm = time.perf_counter()
         mc.decode_host(bits_h, out=rec_h, stream=stream)
+        e2e_step_s.append([round(tm - ts, 4), round(time.perf_counter() - tm, 4)])
+        e2e_iters.append(mc.stats()["cg_iterations_run"])
     e2e_s = time.perf_counter() - t0
+    e2e_clocks = e2e_sampler.stop()
     e2e_value, _ = aggregate(n * F * e2e_steps, e2e_s, world, dist)
     nbytes_pos = pos.nbytes
 
@@ -567,7 +575,9 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": nbytes_pos + mc.stream_bytes,
                     "d2h_bytes_per_step": mc.stream_bytes + nbytes_pos,
-                    "steps": e2e_steps},
+                    "steps": e2e_steps, "encode_decode_s": e2e_step_s,
+                    "cg_iterations": e2e_iters, "clocks": e2e_clocks,
+                    "host_buffers": "pinned (torch pin_memory)"},
             "gpu_launches": launches,
         }
         if world == 1 and not args.no_cpu_baseline:
