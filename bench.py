@@ -53,10 +53,11 @@ WORKLOAD_DEFAULTS = {
 FORM_DEFAULT = {"precision": "fp64", "refine": 0, "anchors": "farthest"}
 # the refined solve's FP64 residual tolerance per workload (else 1e-14): on
 # the 512 x 512 grid a residual of 1e-9 gives the oracle's NMSE to 3e-4
-# relative (bound 1e-2) in 3,520 FP32 iterations a decode with corrections of
+# relative (bound 1e-2) in 3,424 FP32 iterations a decode with corrections of
 # up to 5 decades (each column's last correction stops at what the 1e-9 test
-# still needs; 2 / 3 / 4 / 6 / 7 decades took 4,320 / 4,000 / 3,744 / 3,584 /
-# 3,552); a residual of 1e-11 gave 4e-6 and 1e-14 3e-7 at a higher count
+# still needs; with the stop margin of 0.5 that preceded 0.8, 2 / 3 / 4 / 5 /
+# 6 / 7 decades took 4,320 / 4,000 / 3,744 / 3,520 / 3,584 / 3,552); a
+# residual of 1e-11 gave 4e-6 and 1e-14 3e-7 at a higher count
 # (the last decades sit at the binary64 floor).  The 256 x 256 profiling case
 # keeps 2 decades, the form its profiles were taken in.
 REFINED_RTOL = {"grid512_F300_k64": 1e-9, "grid256_F256_k64": 1e-9}

@@ -132,7 +132,7 @@ typedef struct mesh_codec_params {
                                     r in 1..12 = iterative refinement: the residual of Eq. 12's
                                     normal equations in FP64, FP32 CG corrections solved to a
                                     relative 10^-r (a column whose residual needs less to meet
-                                    cg_rtol stops at that, with a factor-2 margin), until every
+                                    cg_rtol stops at that, with a margin of 0.8), until every
                                     column's FP64 residual meets cg_rtol (FP64 accuracy from
                                     FP32 sweeps, any precision).
                                     In the TF32 / BF16 modes refine > 0 also keeps the

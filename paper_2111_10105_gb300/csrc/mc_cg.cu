@@ -772,7 +772,7 @@ __global__ void k_refine_targets(const double* __restrict__ rr, const double* __
                                  double inner, double* __restrict__ t2, double* cg_bb) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < W; c += gridDim.x * blockDim.x) {
     double t = 0.5;
-    if (!frozen[c] && rr[c] > 0.0) t = fmin(0.5, fmax(inner, 0.5 * rtol * sqrt(bb[c] / rr[c])));
+    if (!frozen[c] && rr[c] > 0.0) t = fmin(0.5, fmax(inner, 0.8 * rtol * sqrt(bb[c] / rr[c])));
     const double q = frozen[c] ? 1.0 : (t / inner) * (t / inner);
     t2[c] = q;
     if (cg_bb) cg_bb[c] *= q;

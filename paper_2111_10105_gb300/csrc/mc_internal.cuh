@@ -235,8 +235,8 @@ void refine_residual(const CgGeom& g, const int32_t* row_ptr, const int32_t* col
 void refine_update(const float* D, long long count, double* X, const int32_t* iters, int W,
                    int32_t* total, cudaStream_t s, Launches& L);
 // Inner target of each column's correction: the relative reduction
-// t = clamp(0.5 rtol ||B|| / ||R||, inner_rtol, 0.5) that brings the FP64
-// residual below rtol ||B|| with a factor-2 margin, so no step solves further
+// t = clamp(0.8 rtol ||B|| / ||R||, inner_rtol, 0.5) that brings the FP64
+// residual below rtol ||B|| with a margin of 0.8, so no step solves further
 // than the outer test needs; t2[col] = (t / inner_rtol)^2 (1 for frozen
 // columns), and cg_bb[col] *= t2[col] when cg_bb is set (the CG's stop test
 // rr <= inner_rtol^2 bb then stops at t)
