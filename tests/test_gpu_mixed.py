@@ -152,3 +152,28 @@ def test_grid316_tf32_against_stored_oracle_nmse():
         for _ in range(2):
             rec = mc.decode(bits).cpu().numpy()
             assert abs(metrics.nmse(pos, rec) - e_o) <= 0.01 * e_o
+
+
+def test_grid512_refined_tf32_against_stored_oracle_nmse():
+    # the 262,144-vertex workload at full size in the form the benchmark times
+    # (TF32 sweeps, FP64-residual refined solve to 1e-9 with FP32 corrections
+    # of up to 5 decades, factored solve, seeded random anchors): the cold
+    # decode (3k + n_c columns) and the decode with the kept anchor response
+    # (3k columns) against the oracle's stored NMSE
+    from synth import config_spec
+    spec = config_spec("grid512_F300_k64")
+    sweeps, e_o = _stored_nmse("grid512_F300_k64")
+    tris, pos = make_sequence(spec)
+    from paper_2111_10105_gb300 import MeshCodec
+    with MeshCodec(tris, pos.shape[1], n_frames=spec.n_frames, rank=spec.rank,
+                   n_anchors=spec.n_anchors, seed=spec.seed, coeff_bits=spec.coeff_bits,
+                   dict_bits=spec.dict_bits, anchor_bits=spec.anchor_bits, oi_sweeps=sweeps,
+                   precision=1, oi_refine_sweeps=1, solve_mode=1, refine=5,
+                   cg_rtol=1e-9) as mc:
+        bits = mc.encode(torch.from_numpy(pos).cuda())
+        for want_cols in (3 * spec.rank + spec.n_anchors, 3 * spec.rank):
+            rec = mc.decode(bits).cpu().numpy()
+            st = mc.stats()
+            assert st["cg_columns"] == (want_cols + 3) // 4 * 4
+            assert st["cg_not_converged"] == 0
+            assert abs(metrics.nmse(pos, rec) - e_o) <= 0.01 * e_o
