@@ -214,6 +214,8 @@ def kernel_work(name, n, W_active, nnz, n_c, eb=8):
     if name == "k_cg_L":
         return e * (dbar + 2), e * 2 * eb + csr + 8 * n
     if name == "k_cg_LT":
+        if eb == 4:   # FP32: K Y, an unweighted neighbour sum (degrees, anchor flags)
+            return e * (dbar + 2) + n_c * W_active, e * 3 * eb + csr + 5 * n
         return e * (2 * dbar + 3) + n_c * W_active, e * 3 * eb + csr + 9 * n
     if name == "k_cg_update":
         return e * 9, e * 6 * eb + 8 * n

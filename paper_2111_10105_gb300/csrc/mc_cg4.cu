@@ -136,38 +136,6 @@ __device__ __forceinline__ float4 gather4(const float* __restrict__ V, const int
   return acc;
 }
 
-// FMA chain sum of w[i] * V[i] over the neighbours, ascending
-__device__ __forceinline__ float4 wgather4(const float* __restrict__ V, const float* __restrict__ w,
-                                           const int32_t* __restrict__ ci, int b, int e, int W,
-                                           int col0) {
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  int p = b;
-  for (; p + 4 <= e; p += 4) {
-    const int c0 = ci[p], c1 = ci[p + 1], c2 = ci[p + 2], c3 = ci[p + 3];
-    const float4 v0 = ld4(V + (long long)c0 * W + col0);
-    const float4 v1 = ld4(V + (long long)c1 * W + col0);
-    const float4 v2 = ld4(V + (long long)c2 * W + col0);
-    const float4 v3 = ld4(V + (long long)c3 * W + col0);
-    const float w0 = w[c0], w1 = w[c1], w2 = w[c2], w3 = w[c3];
-    acc.x = fmaf(w0, v0.x, acc.x); acc.y = fmaf(w0, v0.y, acc.y);
-    acc.z = fmaf(w0, v0.z, acc.z); acc.w = fmaf(w0, v0.w, acc.w);
-    acc.x = fmaf(w1, v1.x, acc.x); acc.y = fmaf(w1, v1.y, acc.y);
-    acc.z = fmaf(w1, v1.z, acc.z); acc.w = fmaf(w1, v1.w, acc.w);
-    acc.x = fmaf(w2, v2.x, acc.x); acc.y = fmaf(w2, v2.y, acc.y);
-    acc.z = fmaf(w2, v2.z, acc.z); acc.w = fmaf(w2, v2.w, acc.w);
-    acc.x = fmaf(w3, v3.x, acc.x); acc.y = fmaf(w3, v3.y, acc.y);
-    acc.z = fmaf(w3, v3.z, acc.z); acc.w = fmaf(w3, v3.w, acc.w);
-  }
-  for (; p < e; ++p) {
-    const int c = ci[p];
-    const float4 v = ld4(V + (long long)c * W + col0);
-    const float wc = w[c];
-    acc.x = fmaf(wc, v.x, acc.x); acc.y = fmaf(wc, v.y, acc.y);
-    acc.z = fmaf(wc, v.z, acc.z); acc.w = fmaf(wc, v.w, acc.w);
-  }
-  return acc;
-}
-
 // The CTA's slice of the adjacency, staged in shared memory when the tile
 // geometry allows it (g.csr_cap > 0): row offsets relative to the block's
 // first entry, then the column indices.  All threads of the CTA take part.
@@ -197,7 +165,7 @@ __device__ __forceinline__ CsrSlice stage_csr(const CgGeom& g, const int32_t* __
   return CsrSlice{row_ptr + r0, col_idx};
 }
 
-// T = L P over one (column tile bx, row block by) of the solve
+// T = L P (Eq. 4) or T = D^-1 L P (Eq. 3) over one (column tile bx, row block by)
 template <int LANES>
 __device__ __forceinline__ void k4_L_body(const CgGeom& g, int bx, int by,
                                           const int32_t* __restrict__ row_ptr,
@@ -216,9 +184,10 @@ __device__ __forceinline__ void k4_L_body(const CgGeom& g, int bx, int by,
     const float4 s = gather4(P, cs.ci, cs.rp[i - r0], cs.rp[i - r0 + 1], g.W, col0);
     const float4 p = ld4(P + i * g.W + col0);
     float4 t;
-    if (kind == 0) {
-      const float a = -inv_d[i];
-      t = make_float4(fmaf(a, s.x, p.x), fmaf(a, s.y, p.y), fmaf(a, s.z, p.z), fmaf(a, s.w, p.w));
+    if (kind == 0) {   // Y = D^-1 (L P): the second pass then needs no weights
+      const float w = inv_d[i], a = -w;
+      t = make_float4(w * fmaf(a, s.x, p.x), w * fmaf(a, s.y, p.y), w * fmaf(a, s.z, p.z),
+                      w * fmaf(a, s.w, p.w));
     } else {
       const float d = (float)deg[i];
       t = make_float4(fmaf(d, p.x, -s.x), fmaf(d, p.y, -s.y), fmaf(d, p.z, -s.z),
@@ -245,7 +214,8 @@ __global__ void __launch_bounds__(LANES * kRowLanes, 2048 / (LANES * kRowLanes))
                    smem_csr);
 }
 
-// Q = L^T T + [anchor] P and the pAp partials over one (column tile, row block)
+// Q = L^T L P + [anchor] P = K T + [anchor] P and the pAp partials over one
+// (column tile, row block), K = D - A
 template <int LANES>
 __device__ __forceinline__ void k4_LT_body(const CgGeom& g, int bx, int by,
                                            const int32_t* __restrict__ row_ptr,
@@ -269,19 +239,15 @@ __device__ __forceinline__ void k4_LT_body(const CgGeom& g, int bx, int by,
   Dot2 pap[4];
   if (valid) {
     for (long long j = r0 + rl; j < r1; j += kRowLanes) {
+      // L^T T = K T (Eq. 4, K = D - A) or, with L = D^-1 K (Eq. 3) and T holding
+      // Y = D^-1 L P, L^T L P = K Y: the same unweighted neighbour sum for both
       const int b = row_ptr[j], e = row_ptr[j + 1];
-      const float4 a = kind == 0 ? wgather4(T, inv_d, col_idx, b, e, g.W, col0)
-                                 : gather4(T, col_idx, b, e, g.W, col0);
+      const float4 a = gather4(T, col_idx, b, e, g.W, col0);
       const float4 t = ld4(T + j * g.W + col0);
       const float4 p = ld4(P + j * g.W + col0);
-      float q[4];
-      if (kind == 0) {
-        q[0] = t.x - a.x; q[1] = t.y - a.y; q[2] = t.z - a.z; q[3] = t.w - a.w;
-      } else {
-        const float d = (float)deg[j];
-        q[0] = fmaf(d, t.x, -a.x); q[1] = fmaf(d, t.y, -a.y);
-        q[2] = fmaf(d, t.z, -a.z); q[3] = fmaf(d, t.w, -a.w);
-      }
+      const float d = (float)deg[j];
+      float q[4] = {fmaf(d, t.x, -a.x), fmaf(d, t.y, -a.y), fmaf(d, t.z, -a.z),
+                    fmaf(d, t.w, -a.w)};
       if (is_anchor[j]) {
         q[0] += p.x; q[1] += p.y; q[2] += p.z; q[3] += p.w;
       }
