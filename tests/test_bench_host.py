@@ -68,7 +68,8 @@ def test_roofline_arithmetic():
     flops = n * W * (2 * 6 + 3) + n_c * W
     assert r["achieved"] == pytest.approx(flops / 0.3e-3 / 1e12, rel=1e-3)
     r = bench.roofline(prof, stats, n, W, nnz, n_c, {"hbm_gbs": 6756.5}, single=True)
-    nbytes = n * W * 3 * 4 + 4 * (n + 1) + 4 * nnz + 9 * n
+    # FP32: the unweighted second pass reads degrees and anchor flags, no 1/d_i
+    nbytes = n * W * 3 * 4 + 4 * (n + 1) + 4 * nnz + 5 * n
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["achieved"] == pytest.approx(nbytes / 0.3e-3 / 1e9, rel=1e-3)
     assert abs(sum(r["time_share"].values()) - 1.0) < 1e-3
